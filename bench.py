@@ -1,0 +1,335 @@
+"""Benchmark of the FDAS hot path: spectra/s at N = 2^21, 85 templates, 8 harmonic planes.
+
+One step is one pass of the whole path over one spectrum: fdas_convolve (overlap-save FT
+convolution into the 85 x 2^21 F-A plane) then fdas_harmonic_sum (harmonic summing, detection,
+compaction). The spectrum is the seeded SKA-sized synthetic workload (4 drifting tones with 8
+harmonics in unit noise). Each rank of a multi-GPU run searches its own spectrum (independent DM
+trials, weak scaling, no collective on the data path).
+
+Prints one JSON line (rank 0). --impl reference times the FP64 CPU oracle instead, as the
+reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FDAS spectra/s, N=2^21, 85 templates, 8 harm: split-BF16 vs FP32; % roofline"
+N_DEFAULT = 1 << 21
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+# FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 flop (FMA) x 2.07 GHz.
+FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+# DRAM bytes per launch from the last ncu capture of each kernel, valid only for the source hash given.
+# (kernel source sha256[:12], read+write bytes per N = 2^21 launch)
+NCU_TRAFFIC = {}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        return float(m["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def src_hash(name):
+    with open(os.path.join(ROOT, "paper_1806_01556_gb300", "csrc", name), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:12]
+
+
+def traffic_for(kernel_file):
+    entry = NCU_TRAFFIC.get(kernel_file)
+    if entry and entry[0] == src_hash(kernel_file):
+        return entry[1]
+    return None
+
+
+def algorithmic(n, n_temp=85, n_tap=421, fft_len=2048, n_harm=8):
+    """Algorithmic work of one spectrum (nominal FFT count 5 F log2 F per transform)."""
+    keep = fft_len - n_tap + 1
+    n_seg = -(-n // keep)
+    fft_flop = 5 * fft_len * int(np.log2(fft_len))
+    conv_flop = fft_flop * n_seg * (1 + n_temp) + 6 * fft_len * n_seg * n_temp + 3 * n_temp * n
+    conv_bytes = n_seg * fft_len * 8 + n_temp * n * 4  # segment reads (with overlap) + plane write
+    hs_bytes = n_temp * n * 4  # every plane point read once
+    return dict(conv_flop=conv_flop, conv_bytes=conv_bytes, hs_bytes=hs_bytes, n_seg=n_seg)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_oracle_sample(wl, sample_bins):
+    """Time the FP64 oracle (overlap-save plane + Algorithm 1) on the first sample_bins bins.
+
+    Returns (seconds per full spectrum, description). The oracle's template bank is built before
+    timing: templates are fixed per parameter set, as on the device.
+    """
+    from oracle import correlate, harmonic, templates, thresholds
+
+    bank = templates.template_bank()
+    ta = thresholds.threshold_array(8, 85)
+    x = wl.spectrum[:sample_bins]
+    t0 = time.perf_counter()
+    plane = correlate.plane_ols(x, bank, 2048)
+    harmonic.detect(plane.astype(np.float32), ta, 8, 0xFF, 200)
+    dt = time.perf_counter() - t0
+    scale = wl.n / sample_bins
+    desc = (f"oracle plane_ols + harmonic.detect on the first {sample_bins} of {wl.n} bins "
+            f"(85 templates, 8 planes), x{scale:g} to one spectrum; numpy, 1 thread")
+    return dt * scale, desc
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import synth
+
+    wl = synth.ska_workload(n=args.n, seed=1)
+    sample = min(args.n, 1 << 17)
+    for _ in range(args.warmup):
+        cpu_oracle_sample(wl, sample)
+    times = []
+    desc = ""
+    for _ in range(args.steps):
+        t, desc = cpu_oracle_sample(wl, sample)
+        times.append(t)
+    sec = float(np.mean(times))
+    value = 1.0 / sec
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "spectra/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args.n),
+        "cpu_baseline": {"value": value, "unit": "spectra/s", "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": "spectra/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(n):
+    return {
+        "workload": f"SKA-sized spectrum N={n} (2^{int(np.log2(n))}), 4 drifting tones x 8 harmonics in unit "
+                    "complex Gaussian noise (seed 1, rank r uses seed 1+r); 85 templates z=-42..42, 421 taps, "
+                    "overlap-save F=2048; 8 harmonic planes, 6-sigma thresholds, 200 candidates per plane",
+        "n": n, "n_temp": 85, "n_tap": 421, "fft_len": 2048, "n_harm": 8, "precision": "fp32",
+        "l2": "inputs larger than L2: the 713 MB plane is written and read every step",
+        "parallelism": "replicas (one spectrum per GPU, no collective)",
+    }
+
+
+def run_fdas(args):
+    import torch
+
+    import paper_1806_01556_gb300 as fdas
+    import synth
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    wl = synth.ska_workload(n=args.n, seed=1 + rank)
+    # The CPU baseline runs before any timed GPU work (rank 0, N = 1 only).
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sec, desc = cpu_oracle_sample(wl, min(args.n, 1 << 19))
+        cpu = {"value": 1.0 / sec, "unit": "spectra/s", "cores": 1, "kind": "oracle", "sample": desc}
+
+    p = fdas.Params()
+    s = fdas.Searcher(p, args.n, device=f"cuda:{local}")
+    d_spec = torch.from_numpy(wl.spectrum).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    ld = s.ld
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        fdas.fdas_convolve(p, d_spec, args.n, s.tmpl, s.plane, ld, stream)
+        if ev is not None:
+            ev[1].record(stream)
+        fdas.fdas_harmonic_sum(p, s.plane, args.n, ld, s.thresh, s.cands, s.counts, s.peaks, s.ws, s.ws_bytes,
+                               stream)
+        if ev is not None:
+            ev[2].record(stream)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+
+    events = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(local)
+    with sampler:
+        barrier()
+        torch.cuda.synchronize(dev)
+        start.record(stream)
+        for k in range(args.steps):
+            step(events[k])
+        end.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+    total_ms = start.elapsed_time(end)
+    conv_ms = [e[0].elapsed_time(e[1]) for e in events]
+    hs_ms = [e[1].elapsed_time(e[2]) for e in events]
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * args.steps / (total_ms / 1e3)
+
+    # End to end through fdas_search_host: pinned host spectrum in, candidates out, every step.
+    h_spec = torch.from_numpy(wl.spectrum).pin_memory()
+    for _ in range(2):
+        s.search_host(h_spec, args.n)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.search_host(h_spec, args.n)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    cands, counts, _ = s.results(host=True)
+
+    if rank == 0:
+        alg = algorithmic(args.n)
+        conv_avg = float(np.mean(conv_ms)) / 1e3
+        hs_avg = float(np.mean(hs_ms)) / 1e3
+        hbm, hbm_kind = peaks()
+        conv_tflops = alg["conv_flop"] / conv_avg / 1e12
+        hs_gbs = alg["hs_bytes"] / hs_avg / 1e9
+        stages = {
+            "convolve": {"ms": conv_avg * 1e3, "bound": "alu", "achieved": conv_tflops, "unit": "TFLOP/s",
+                         "peak": FP32_PEAK_TFLOPS, "frac": conv_tflops / FP32_PEAK_TFLOPS,
+                         "hbm_gbs": alg["conv_bytes"] / conv_avg / 1e9,
+                         "traffic": traffic_for("convolve.cu")},
+            "harmonic_sum": {"ms": hs_avg * 1e3, "bound": "hbm", "achieved": hs_gbs, "unit": "GB/s", "peak": hbm,
+                             "frac": hs_gbs / hbm, "traffic": traffic_for("harmonic.cu")},
+        }
+        dom = "convolve" if conv_avg >= hs_avg else "harmonic_sum"
+        d = stages[dom]
+        roof = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
+                "frac": d["frac"], "traffic": d["traffic"],
+                "peak_source": ("152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz" if dom == "convolve"
+                                else f"MEASURED_PEAKS.json hbm_gbs ({hbm_kind})")}
+        d2h = p.n_harm * p.cand_cap * 12 + p.n_harm * 4 + p.n_harm * 12
+        line = {
+            "metric": METRIC, "value": value, "unit": "spectra/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(args.n),
+            "fa_points_per_s": value * 85 * args.n,
+            "clocks": sampler.summary(),
+            "e2e": {"value": world * args.steps / e2e_s, "unit": "spectra/s",
+                    "h2d_bytes_per_step": args.n * 8, "d2h_bytes_per_step": d2h},
+            "gpu_launches": 4 * args.steps,
+            "roofline": roof,
+            "stages": stages,
+            "cpu_baseline": cpu,
+            "candidates_per_plane": [int(c) for c in counts],
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="fdas", choices=["fdas", "reference"])
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_fdas(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,209 @@
+/*
+ * fdas.h - C ABI of the FDAS hot path on one GB300 (sm_103a).
+ *
+ * The Fourier-domain acceleration search (FDAS) module of Wang, Thiagaraj and Sinnen,
+ * "Combining Multiple Optimized FPGA-based Pulsar Search Modules Using OpenCL", has two stages
+ * (Sec. 2 and Sec. 3.1, Eq. t_FDAS):
+ *   1. FT convolution. One complex input spectrum is correlated with N_temp acceleration
+ *      templates of N_tap taps by overlap-save (Sec. 2.1). The power |y|^2 of each output forms
+ *      the filter-output plane (FOP), here called the F-A plane.
+ *   2. Harmonic summing with threshold detection over that plane (Sec. 2.2, Algorithm 1),
+ *      which yields a candidate list per harmonic plane.
+ *
+ * Conventions for every call below:
+ *   - Pointers named d_* are device pointers and h_* are host pointers. The caller owns every
+ *     buffer, and no call allocates device memory.
+ *   - Device buffers must be 16-byte aligned. cudaMalloc gives 256 bytes.
+ *   - Calls that take a stream enqueue work on it and return without waiting, except
+ *     fdas_search_host. A CUDA error seen at launch is returned as FDAS_ERR_CUDA. An error that
+ *     happens later on the device shows up at the caller's next synchronisation.
+ *   - Arguments are checked before any work is enqueued. A bad argument returns a negative
+ *     status and enqueues nothing.
+ *   - Complex values are interleaved float pairs (re, im), "complex64".
+ *   - stream is a cudaStream_t. NULL means the legacy default stream.
+ */
+#ifndef FDAS_H
+#define FDAS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *fdas_stream_t; /* same type as cudaStream_t */
+
+typedef int fdas_status;
+#define FDAS_OK 0
+#define FDAS_ERR_INVALID_ARG (-1) /* null/misaligned pointer, size out of range, bad params     */
+#define FDAS_ERR_UNSUPPORTED (-2) /* valid parameters this build has no kernel for             */
+#define FDAS_ERR_WORKSPACE (-3)   /* workspace smaller than fdas_workspace_bytes()             */
+#define FDAS_ERR_CUDA (-4)        /* a CUDA runtime call or kernel launch failed               */
+
+/* Arithmetic of the FT convolution. Only FDAS_FP32 has kernels in this build. */
+#define FDAS_FP32 0
+#define FDAS_BF16X3 1
+#define FDAS_FP16S 2
+
+/* Largest supported spectrum length. Candidate keys pack the column j into 24 bits. */
+#define FDAS_MAX_N (1u << 24)
+/* Per harmonic plane, up to this many threshold crossings are kept for the top-cand_cap
+ * selection. Beyond it, counts[] still counts every crossing, but the kept set is whichever
+ * crossings arrived first on the device, so the top-cand_cap choice is no longer exact. */
+#define FDAS_RAW_CAP 16384
+#define FDAS_MAX_CAND_CAP 4096
+#define FDAS_MAX_HARM 16
+
+/*
+ * Search parameters (the paper's parameter table in Sec. 2, "FDAS Module Parameters").
+ *   n_temp    N_temp, number of templates = plane rows. Odd, 3..255. Default 85.
+ *   z_min     drift of template 0 in Fourier bins. The grid must be symmetric:
+ *             z_min = -(n_temp-1)/2 * z_step. Default -42.
+ *   z_step    drift step between templates, >= 1. Default 1. Template t has z_t = z_min + t*z_step.
+ *   n_tap     N_tap, taps per template. Odd, 3..fft_len/2. Default 421.
+ *   fft_len   overlap-save segment length F (AOLS-2048 in Sec. 2.1). Only 2048 in this build.
+ *   n_harm    N_hp, harmonic planes summed, 1..16. Default 8.
+ *   harm_mask bit k-1 set: report candidates of HP_k. Nonzero, no bit at or above n_harm.
+ *   cand_cap  N_cand, candidates kept per reported plane, 1..4096. Default 200.
+ *   precision FDAS_FP32.
+ */
+typedef struct {
+    int32_t n_temp;
+    int32_t z_min;
+    int32_t z_step;
+    int32_t n_tap;
+    int32_t fft_len;
+    int32_t n_harm;
+    uint32_t harm_mask;
+    int32_t cand_cap;
+    int32_t precision;
+} fdas_params;
+
+/* One candidate: HP_k(i, j) = power > TA(k, i). i is the fundamental's template offset from the
+ * zero-drift row (drift z = i*z_step), j its column (Fourier bin), k the harmonic plane (1-based). */
+typedef struct {
+    float power;
+    uint32_t j;
+    int16_t i;
+    uint8_t k;
+    uint8_t pad;
+} fdas_cand;
+
+/* Fill *p with the defaults above (85 templates, z = -42..42, 421 taps, F = 2048, 8 planes,
+ * all reported, 200 candidates, FP32). */
+void fdas_default_params(fdas_params *p);
+
+/* FDAS_OK if *p is valid and this build has kernels for it. Otherwise FDAS_ERR_INVALID_ARG or
+ * FDAS_ERR_UNSUPPORTED. */
+fdas_status fdas_check_params(const fdas_params *p);
+
+/* Human-readable name of a status code. The string is static. */
+const char *fdas_status_string(fdas_status s);
+
+/* Size of the template bank written by fdas_make_templates: (n_temp + 1) * fft_len * 8 bytes.
+ * Returns 0 for invalid parameters. */
+size_t fdas_templates_bytes(const fdas_params *p);
+
+/* Size of a plane of n columns with row stride ld (floats): n_temp * ld * 4 bytes. */
+size_t fdas_plane_bytes(const fdas_params *p, size_t n, size_t ld);
+
+/* Device workspace needed by fdas_harmonic_sum and fdas_search for a spectrum of n bins.
+ * It holds candidate counters, per-plane peaks and up to FDAS_RAW_CAP raw candidate keys per
+ * plane: 8 * n_harm * (FDAS_RAW_CAP + 4) bytes. Returns 0 for invalid parameters. */
+size_t fdas_workspace_bytes(const fdas_params *p, size_t n);
+
+/*
+ * Threshold array TA(k, i) of Algorithm 1 (Sec. 2.2), computed on the host.
+ * Row k-1 (k = 1..n_harm) holds the threshold of HP_k for every row offset i:
+ * h_thresh[(k-1)*n_temp + (i + (n_temp-1)/2)].
+ *   kind 0: the x with P(Gamma(k,1) > x) = Q(sigma), the one-sided Gaussian tail at sigma. For
+ *           integer k, P(Gamma(k,1) > x) = exp(-x) sum_{m<k} x^m/m!. This is the false-alarm
+ *           rate of a sum of k unit-mean exponential powers.
+ *   kind 1: mean + sigma*sd = k + sigma*sqrt(k).
+ * The value is computed in double precision and rounded to float. h_thresh holds
+ * n_harm*n_temp floats.
+ */
+fdas_status fdas_default_thresholds(const fdas_params *p, double sigma, int kind, float *h_thresh);
+
+/*
+ * Template bank (FIR coefficients of the FT convolution; Sec. 2.1, 85 filters of 421 taps).
+ * The paper does not define the kernel. This library uses the Fourier response of a linearly
+ * drifting tone, indexed by mean frequency:
+ *     A_z(q) = integral_0^1 exp(2 pi i (-(q + z/2) tau + z tau^2/2)) d tau,
+ * evaluated in double precision on the device (composite 16-point Gauss-Legendre quadrature).
+ * Template t uses z_t = z_min + t*z_step and taps a_t[q] = A_{z_t}(q), q = -h..h, with
+ * h = (n_tap-1)/2.
+ * d_tmpl (fdas_templates_bytes bytes, complex64) receives:
+ *   rows t = 0..n_temp-1: T_t[m] = conj( sum_q a_t[q] exp(-2 pi i m q / F) ), m = 0..F-1.
+ *                         This is the DFT (Eq. 2) of the taps placed wrapped in a length-F array.
+ *   row n_temp:           the twiddle table w[k] = exp(-2 pi i k / F), k = 0..F-1.
+ * The DFT and the twiddles are computed in double precision and rounded once to float.
+ * The bank is read-only input to fdas_convolve and fdas_search.
+ */
+fdas_status fdas_make_templates(const fdas_params *p, void *d_tmpl, fdas_stream_t stream);
+
+/*
+ * FT convolution by overlap-save (Sec. 2.1: OLS-FDFIR, AOLS-2048-P with power), producing the
+ * F-A plane:
+ *     P[t][j] = | sum_{q=-h}^{h} X[j+q] conj(a_t[q]) |^2,  X = 0 outside [0, n),
+ * for t = 0..n_temp-1 and j = 0..n-1.
+ * Each segment of F input points (overlap n_tap-1) is transformed once, multiplied by every
+ * template and transformed back. Only the L = F - n_tap + 1 valid outputs per segment are
+ * stored, so the paper's "discard" step of the FOP preparation (Sec. 3.2) is fused into the store.
+ *   d_spec  complex64[n], the input spectrum. 1 <= n <= FDAS_MAX_N.
+ *   d_tmpl  bank from fdas_make_templates with the same parameters.
+ *   d_plane float32[n_temp][ld], ld >= n. Columns n..ld-1 are not written.
+ * Arithmetic is float32 with float32 FFTs.
+ */
+fdas_status fdas_convolve(const fdas_params *p, const void *d_spec, size_t n, const void *d_tmpl,
+                          float *d_plane, size_t ld, fdas_stream_t stream);
+
+/*
+ * Harmonic summing with threshold detection (Sec. 2.2, Algorithm 1), with the stretch read by
+ * fundamental:
+ *     HP_k(i, j) = sum_{l=1}^{k} P[c + l*i][l*j],  c = (n_temp-1)/2,
+ * on the domain |k*i| <= c, k*j <= n-1. The sum is float32, running in the order l = 1, 2, ..., k.
+ * A point is a candidate of plane k when bit k-1 of harm_mask is set and
+ * HP_k(i, j) > d_thresh[(k-1)*n_temp + c + i] (strict, float32).
+ *   d_plane  float32[n_temp][ld], e.g. from fdas_convolve.
+ *   d_thresh float32[n_harm][n_temp] (see fdas_default_thresholds).
+ *   d_cands  fdas_cand[n_harm][cand_cap]. Slot k-1 receives the top min(counts[k-1], cand_cap)
+ *            crossings of HP_k in canonical order: power descending, then i, then j ascending.
+ *            Slots past that are not written.
+ *   d_counts uint32[n_harm]: total crossings per plane (0 for planes not reported).
+ *   d_peaks  fdas_cand[n_harm] or NULL: the first point of each HP_k in canonical order,
+ *            whether or not it crosses the threshold.
+ *   d_ws     workspace of at least fdas_workspace_bytes(p, n) bytes, used for counters and raw
+ *            candidate keys. Its contents need no initialisation.
+ * Calls that share d_ws must not overlap on the device.
+ */
+fdas_status fdas_harmonic_sum(const fdas_params *p, const float *d_plane, size_t n, size_t ld,
+                              const float *d_thresh, fdas_cand *d_cands, uint32_t *d_counts,
+                              fdas_cand *d_peaks, void *d_ws, size_t ws_bytes, fdas_stream_t stream);
+
+/* fdas_convolve followed by fdas_harmonic_sum on the same stream: the whole FDAS path for one
+ * spectrum (Sec. 3.1, Eq. t_FDAS, with no separate FOP preparation). */
+fdas_status fdas_search(const fdas_params *p, const void *d_spec, size_t n, const void *d_tmpl,
+                        float *d_plane, size_t ld, const float *d_thresh, fdas_cand *d_cands,
+                        uint32_t *d_counts, fdas_cand *d_peaks, void *d_ws, size_t ws_bytes,
+                        fdas_stream_t stream);
+
+/*
+ * fdas_search with the spectrum and the results in host memory: the end-to-end call.
+ * It copies h_spec (complex64[n], pinned memory recommended) into d_spec, runs fdas_search,
+ * copies the candidates, counts and (if h_peaks is not NULL) peaks back to the host, and waits
+ * for the stream. d_cands, d_counts and d_peaks are device staging buffers of the same shapes as
+ * in fdas_harmonic_sum (d_peaks may be NULL only if h_peaks is NULL).
+ */
+fdas_status fdas_search_host(const fdas_params *p, const void *h_spec, size_t n, void *d_spec,
+                             const void *d_tmpl, float *d_plane, size_t ld, const float *d_thresh,
+                             fdas_cand *d_cands, uint32_t *d_counts, fdas_cand *d_peaks,
+                             fdas_cand *h_cands, uint32_t *h_counts, fdas_cand *h_peaks, void *d_ws,
+                             size_t ws_bytes, fdas_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FDAS_H */

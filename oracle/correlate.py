@@ -65,8 +65,8 @@ def power_at(spectrum: np.ndarray, bank: np.ndarray, rows: np.ndarray, cols: np.
     return out
 
 
-def correlate_ols(spectrum: np.ndarray, bank: np.ndarray, fft_len: int) -> np.ndarray:
-    """y[t][j] by overlap-save (Sec. 2.1) on the causal filter, with the oracle's own FFT."""
+def _ols_rows(spectrum: np.ndarray, bank: np.ndarray, fft_len: int):
+    """Yield (t, y_t) by overlap-save (Sec. 2.1) on the causal filter, with the oracle's own FFT."""
     x = np.asarray(spectrum, dtype=np.complex128)
     n = x.shape[0]
     n_temp, n_tap = bank.shape
@@ -78,7 +78,7 @@ def correlate_ols(spectrum: np.ndarray, bank: np.ndarray, fft_len: int) -> np.nd
     # Causal outputs needed: i = j + h for j = 0..N-1, i.e. i in [h, N + h).
     n_causal = n + h
     n_chunk = -(-n_causal // keep)
-    # Step 1: chunk c covers causal inputs i - (N_tap - 1) .. for outputs i in [c*L, c*L + L).
+    # Step 1: chunk c holds the inputs of causal outputs i in [c*L, c*L + L), starting N_tap-1 earlier.
     padded = np.concatenate(
         [np.zeros(n_tap - 1, np.complex128), x, np.zeros(n_chunk * keep + f, np.complex128)]
     )
@@ -89,17 +89,25 @@ def correlate_ols(spectrum: np.ndarray, bank: np.ndarray, fft_len: int) -> np.nd
     g = np.zeros((n_temp, f), dtype=np.complex128)
     g[:, :n_tap] = np.conj(bank[:, ::-1])
     spec_g = fft(g)
-    y = np.empty((n_temp, n), dtype=np.complex128)
     for t in range(n_temp):
         # Step 2: multiply and transform back.
         out = fft(spec_chunks * spec_g[t][None, :], inverse=True)
         # Step 3: discard the first N_tap - 1 outputs of every chunk.
         causal = out[:, n_tap - 1 :].reshape(-1)[:n_causal]
-        y[t] = causal[h : h + n]
+        yield t, causal[h : h + n]
+
+
+def correlate_ols(spectrum: np.ndarray, bank: np.ndarray, fft_len: int) -> np.ndarray:
+    """y[t][j] by overlap-save (Sec. 2.1), complex128[n_temp][N]."""
+    y = np.empty((bank.shape[0], len(spectrum)), dtype=np.complex128)
+    for t, row in _ols_rows(spectrum, bank, fft_len):
+        y[t] = row
     return y
 
 
 def plane_ols(spectrum: np.ndarray, bank: np.ndarray, fft_len: int) -> np.ndarray:
     """P[t][j] = |y_t[j]|^2 from the overlap-save route, float64[n_temp][N]."""
-    y = correlate_ols(spectrum, bank, fft_len)
-    return y.real**2 + y.imag**2
+    p = np.empty((bank.shape[0], len(spectrum)), dtype=np.float64)
+    for t, row in _ols_rows(spectrum, bank, fft_len):
+        p[t] = row.real**2 + row.imag**2
+    return p

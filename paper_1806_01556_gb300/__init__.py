@@ -1,0 +1,229 @@
+"""Python binding of libfdas, the FDAS hot path on one GB300 (sm_103a).
+
+The functions here have the names of the C entry points in include/fdas.h and only marshal
+arguments: torch tensors are passed as device pointers, and the current torch CUDA stream as the
+cudaStream_t. Every step of the path runs in the library's CUDA kernels. PyTorch only provides
+device memory and streams. If libfdas.so is missing, the first call raises ImportError;
+nothing falls back to the CPU.
+
+``Searcher`` bundles the buffers one spectrum length needs (template bank, plane, workspace,
+thresholds, candidate outputs) and runs ``fdas_search`` or ``fdas_search_host`` on them.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import asdict, dataclass
+
+import numpy as np
+
+from . import _lib
+
+__all__ = [
+    "FdasError",
+    "Params",
+    "CAND_DTYPE",
+    "lib",
+    "fdas_check_params",
+    "fdas_templates_bytes",
+    "fdas_plane_bytes",
+    "fdas_workspace_bytes",
+    "fdas_default_thresholds",
+    "fdas_make_templates",
+    "fdas_convolve",
+    "fdas_harmonic_sum",
+    "fdas_search",
+    "fdas_search_host",
+    "decode_cands",
+    "Searcher",
+]
+
+# Host view of fdas_cand (12 bytes): power, j, i, k, pad.
+CAND_DTYPE = np.dtype([("power", "<f4"), ("j", "<u4"), ("i", "<i2"), ("k", "u1"), ("pad", "u1")])
+assert CAND_DTYPE.itemsize == C.sizeof(_lib.fdas_cand)
+
+
+class FdasError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        msg = lib().fdas_status_string(status).decode()
+        super().__init__(f"{what}: {msg} ({status})")
+        self.status = status
+
+
+def lib() -> C.CDLL:
+    return _lib.load()
+
+
+@dataclass
+class Params:
+    """Search parameters; the fields of fdas_params (see include/fdas.h)."""
+
+    n_temp: int = 85
+    z_min: int = -42
+    z_step: int = 1
+    n_tap: int = 421
+    fft_len: int = 2048
+    n_harm: int = 8
+    harm_mask: int = 0xFF
+    cand_cap: int = 200
+    precision: int = _lib.FDAS_FP32
+
+    def c(self) -> _lib.fdas_params:
+        return _lib.fdas_params(**asdict(self))
+
+
+def _ptr(t) -> C.c_void_p:
+    if t is None:
+        return C.c_void_p(0)
+    if isinstance(t, np.ndarray):
+        return C.c_void_p(t.ctypes.data)
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> C.c_void_p:
+    if stream is None:
+        import torch
+
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _check(status: int, what: str) -> None:
+    if status != _lib.FDAS_OK:
+        raise FdasError(status, what)
+
+
+def fdas_check_params(p: Params) -> int:
+    return lib().fdas_check_params(C.byref(p.c()))
+
+
+def fdas_templates_bytes(p: Params) -> int:
+    return lib().fdas_templates_bytes(C.byref(p.c()))
+
+
+def fdas_plane_bytes(p: Params, n: int, ld: int) -> int:
+    return lib().fdas_plane_bytes(C.byref(p.c()), n, ld)
+
+
+def fdas_workspace_bytes(p: Params, n: int) -> int:
+    return lib().fdas_workspace_bytes(C.byref(p.c()), n)
+
+
+def fdas_default_thresholds(p: Params, sigma: float = 6.0, kind: int = 0) -> np.ndarray:
+    """TA as float32[n_harm][n_temp], computed by the library on the host."""
+    out = np.empty((p.n_harm, p.n_temp), dtype=np.float32)
+    _check(lib().fdas_default_thresholds(C.byref(p.c()), sigma, kind, _ptr(out)), "fdas_default_thresholds")
+    return out
+
+
+def fdas_make_templates(p: Params, d_tmpl, stream=None) -> None:
+    _check(lib().fdas_make_templates(C.byref(p.c()), _ptr(d_tmpl), _stream(stream)), "fdas_make_templates")
+
+
+def fdas_convolve(p: Params, d_spec, n: int, d_tmpl, d_plane, ld: int, stream=None) -> None:
+    _check(
+        lib().fdas_convolve(C.byref(p.c()), _ptr(d_spec), n, _ptr(d_tmpl), _ptr(d_plane), ld, _stream(stream)),
+        "fdas_convolve",
+    )
+
+
+def fdas_harmonic_sum(p: Params, d_plane, n, ld, d_thresh, d_cands, d_counts, d_peaks, d_ws, ws_bytes, stream=None):
+    _check(
+        lib().fdas_harmonic_sum(
+            C.byref(p.c()), _ptr(d_plane), n, ld, _ptr(d_thresh), _ptr(d_cands), _ptr(d_counts), _ptr(d_peaks),
+            _ptr(d_ws), ws_bytes, _stream(stream),
+        ),
+        "fdas_harmonic_sum",
+    )
+
+
+def fdas_search(p: Params, d_spec, n, d_tmpl, d_plane, ld, d_thresh, d_cands, d_counts, d_peaks, d_ws, ws_bytes,
+                stream=None):
+    _check(
+        lib().fdas_search(
+            C.byref(p.c()), _ptr(d_spec), n, _ptr(d_tmpl), _ptr(d_plane), ld, _ptr(d_thresh), _ptr(d_cands),
+            _ptr(d_counts), _ptr(d_peaks), _ptr(d_ws), ws_bytes, _stream(stream),
+        ),
+        "fdas_search",
+    )
+
+
+def fdas_search_host(p: Params, h_spec, n, d_spec, d_tmpl, d_plane, ld, d_thresh, d_cands, d_counts, d_peaks,
+                     h_cands, h_counts, h_peaks, d_ws, ws_bytes, stream=None):
+    _check(
+        lib().fdas_search_host(
+            C.byref(p.c()), _ptr(h_spec), n, _ptr(d_spec), _ptr(d_tmpl), _ptr(d_plane), ld, _ptr(d_thresh),
+            _ptr(d_cands), _ptr(d_counts), _ptr(d_peaks), _ptr(h_cands), _ptr(h_counts), _ptr(h_peaks), _ptr(d_ws),
+            ws_bytes, _stream(stream),
+        ),
+        "fdas_search_host",
+    )
+
+
+def decode_cands(raw: np.ndarray, counts: np.ndarray, cand_cap: int) -> list[np.ndarray]:
+    """Split the cand buffer (n_harm * cand_cap records) into per-plane arrays of the written length."""
+    rec = np.ascontiguousarray(raw).view(CAND_DTYPE).reshape(len(counts), cand_cap)
+    return [rec[k, : min(int(counts[k]), cand_cap)].copy() for k in range(len(counts))]
+
+
+def round_up(x: int, m: int) -> int:
+    return (x + m - 1) // m * m
+
+
+class Searcher:
+    """Device buffers for spectra of up to ``n_max`` bins, allocated once with torch.
+
+    The template bank is generated on the device at construction (fdas_make_templates). The
+    thresholds default to the library's 6-sigma table, or an explicit float32[n_harm][n_temp]
+    array can be given.
+    """
+
+    def __init__(self, params: Params, n_max: int, thresh: np.ndarray | None = None, device: str = "cuda:0"):
+        import torch
+
+        st = fdas_check_params(params)
+        if st != _lib.FDAS_OK:
+            raise FdasError(st, "params")
+        self.p = params
+        self.n_max = n_max
+        self.ld = round_up(n_max, 64)
+        self.device = torch.device(device)
+        u8 = dict(dtype=torch.uint8, device=self.device)
+        self.tmpl = torch.empty(fdas_templates_bytes(params), **u8)
+        self.plane = torch.empty((params.n_temp, self.ld), dtype=torch.float32, device=self.device)
+        self.ws_bytes = fdas_workspace_bytes(params, n_max)
+        self.ws = torch.empty(self.ws_bytes, **u8)
+        self.spec = torch.empty(n_max, dtype=torch.complex64, device=self.device)
+        ta = fdas_default_thresholds(params) if thresh is None else np.ascontiguousarray(thresh, dtype=np.float32)
+        self.thresh_host = ta
+        self.thresh = torch.from_numpy(ta).to(self.device)
+        nrec = params.n_harm * params.cand_cap
+        self.cands = torch.empty(nrec * CAND_DTYPE.itemsize, **u8)
+        self.counts = torch.empty(params.n_harm, dtype=torch.int32, device=self.device)
+        self.peaks = torch.empty(params.n_harm * CAND_DTYPE.itemsize, **u8)
+        self.h_cands = torch.empty(nrec * CAND_DTYPE.itemsize, dtype=torch.uint8, pin_memory=True)
+        self.h_counts = torch.empty(params.n_harm, dtype=torch.int32, pin_memory=True)
+        self.h_peaks = torch.empty(params.n_harm * CAND_DTYPE.itemsize, dtype=torch.uint8, pin_memory=True)
+        with torch.cuda.device(self.device):
+            fdas_make_templates(params, self.tmpl)
+
+    def search(self, spec, n: int | None = None, stream=None) -> None:
+        """Run fdas_search on a device complex64 tensor (results stay on the device)."""
+        n = spec.numel() if n is None else n
+        fdas_search(self.p, spec, n, self.tmpl, self.plane, self.ld, self.thresh, self.cands, self.counts,
+                    self.peaks, self.ws, self.ws_bytes, stream)
+
+    def search_host(self, h_spec, n: int | None = None, stream=None) -> None:
+        """Run fdas_search_host on a host complex64 buffer (pinned torch tensor or numpy array)."""
+        n = (h_spec.numel() if hasattr(h_spec, "numel") else h_spec.size) if n is None else n
+        fdas_search_host(self.p, h_spec, n, self.spec, self.tmpl, self.plane, self.ld, self.thresh, self.cands,
+                         self.counts, self.peaks, self.h_cands, self.h_counts, self.h_peaks, self.ws, self.ws_bytes,
+                         stream)
+
+    def results(self, host: bool = False):
+        """(per-plane candidate arrays, counts, peaks) as numpy, from the device or host buffers."""
+        if host:
+            raw, counts, peaks = self.h_cands.numpy(), self.h_counts.numpy(), self.h_peaks.numpy()
+        else:
+            raw, counts, peaks = self.cands.cpu().numpy(), self.counts.cpu().numpy(), self.peaks.cpu().numpy()
+        counts = counts.astype(np.uint32)
+        return decode_cands(raw, counts, self.p.cand_cap), counts, peaks.view(CAND_DTYPE).copy()

@@ -1,0 +1,196 @@
+// C ABI entry points of libfdas: argument checks, workspace carving and kernel launches.
+// Declarations and the full contract of each call are in include/fdas.h.
+#include <cmath>
+#include <cstring>
+
+#include "fdas_internal.cuh"
+
+using fdas::Geometry;
+
+namespace {
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+fdas_status check_shape(const fdas_params *p, size_t n, size_t ld) {
+    if (n < 1 || n > FDAS_MAX_N || ld < n) return FDAS_ERR_INVALID_ARG;
+    if ((unsigned long long)ld * (unsigned long long)p->n_temp > (1ull << 40)) return FDAS_ERR_INVALID_ARG;
+    return FDAS_OK;
+}
+
+fdas_status cuda_status(cudaError_t e) { return e == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA; }
+
+// S_k(x) = P(Gamma(k,1) > x) = exp(-x) sum_{m<k} x^m / m!, integer k >= 1.
+double gamma_survival(int k, double x) {
+    double term = 1.0, total = 1.0;
+    for (int m = 1; m < k; ++m) {
+        term *= x / m;
+        total += term;
+    }
+    return std::exp(-x) * total;
+}
+
+// The x > 0 with S_k(x) = p, by bisection (S_k decreases strictly from 1 to 0).
+double gamma_threshold(int k, double p) {
+    double lo = 0.0, hi = 1.0;
+    while (gamma_survival(k, hi) > p) hi *= 2.0;
+    for (int it = 0; it < 400 && hi - lo > 1e-15 * hi; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (gamma_survival(k, mid) > p)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+}  // namespace
+
+extern "C" {
+
+void fdas_default_params(fdas_params *p) {
+    if (!p) return;
+    p->n_temp = 85;
+    p->z_min = -42;
+    p->z_step = 1;
+    p->n_tap = 421;
+    p->fft_len = 2048;
+    p->n_harm = 8;
+    p->harm_mask = 0xFFu;
+    p->cand_cap = 200;
+    p->precision = FDAS_FP32;
+}
+
+fdas_status fdas_check_params(const fdas_params *p) {
+    if (!p) return FDAS_ERR_INVALID_ARG;
+    if (p->n_temp < 3 || p->n_temp > 255 || (p->n_temp & 1) == 0) return FDAS_ERR_INVALID_ARG;
+    if (p->z_step < 1 || p->z_step > 1024) return FDAS_ERR_INVALID_ARG;
+    if ((long long)p->z_min != -(long long)((p->n_temp - 1) / 2) * p->z_step) return FDAS_ERR_INVALID_ARG;
+    if (p->fft_len < 64 || p->fft_len > 8192 || (p->fft_len & (p->fft_len - 1)) != 0) return FDAS_ERR_INVALID_ARG;
+    if (p->n_tap < 3 || (p->n_tap & 1) == 0 || p->n_tap > p->fft_len / 2) return FDAS_ERR_INVALID_ARG;
+    if (p->n_harm < 1 || p->n_harm > FDAS_MAX_HARM) return FDAS_ERR_INVALID_ARG;
+    if (p->harm_mask == 0u || (p->n_harm < 32 && (p->harm_mask >> p->n_harm) != 0u)) return FDAS_ERR_INVALID_ARG;
+    if (p->cand_cap < 1 || p->cand_cap > FDAS_MAX_CAND_CAP) return FDAS_ERR_INVALID_ARG;
+    if (p->precision != FDAS_FP32 && p->precision != FDAS_BF16X3 && p->precision != FDAS_FP16S)
+        return FDAS_ERR_INVALID_ARG;
+    if (p->fft_len != 2048 || p->precision != FDAS_FP32) return FDAS_ERR_UNSUPPORTED;
+    return FDAS_OK;
+}
+
+const char *fdas_status_string(fdas_status s) {
+    switch (s) {
+        case FDAS_OK: return "ok";
+        case FDAS_ERR_INVALID_ARG: return "invalid argument";
+        case FDAS_ERR_UNSUPPORTED: return "unsupported parameters";
+        case FDAS_ERR_WORKSPACE: return "workspace too small";
+        case FDAS_ERR_CUDA: return "CUDA error";
+        default: return "unknown status";
+    }
+}
+
+size_t fdas_templates_bytes(const fdas_params *p) {
+    if (fdas_check_params(p) == FDAS_ERR_INVALID_ARG) return 0;
+    return (size_t)(p->n_temp + 1) * (size_t)p->fft_len * 8u;
+}
+
+size_t fdas_plane_bytes(const fdas_params *p, size_t n, size_t ld) {
+    if (fdas_check_params(p) == FDAS_ERR_INVALID_ARG || ld < n) return 0;
+    return (size_t)p->n_temp * ld * 4u;
+}
+
+size_t fdas_workspace_bytes(const fdas_params *p, size_t n) {
+    (void)n;
+    if (fdas_check_params(p) == FDAS_ERR_INVALID_ARG) return 0;
+    return fdas::hs_workspace_words(p->n_harm) * 8u;
+}
+
+fdas_status fdas_default_thresholds(const fdas_params *p, double sigma, int kind, float *h_thresh) {
+    fdas_status st = fdas_check_params(p);
+    if (st == FDAS_ERR_INVALID_ARG) return st;
+    if (!h_thresh || !(sigma > 0.0) || sigma > 30.0 || (kind != 0 && kind != 1)) return FDAS_ERR_INVALID_ARG;
+    const double tail = 0.5 * std::erfc(sigma / std::sqrt(2.0));
+    for (int k = 1; k <= p->n_harm; ++k) {
+        const double v = kind == 0 ? gamma_threshold(k, tail) : k + sigma * std::sqrt((double)k);
+        for (int t = 0; t < p->n_temp; ++t) h_thresh[(size_t)(k - 1) * p->n_temp + t] = (float)v;
+    }
+    return FDAS_OK;
+}
+
+fdas_status fdas_make_templates(const fdas_params *p, void *d_tmpl, fdas_stream_t stream) {
+    fdas_status st = fdas_check_params(p);
+    if (st != FDAS_OK) return st;
+    if (!d_tmpl || !aligned16(d_tmpl)) return FDAS_ERR_INVALID_ARG;
+    return cuda_status(fdas::launch_templates(*p, d_tmpl, stream));
+}
+
+fdas_status fdas_convolve(const fdas_params *p, const void *d_spec, size_t n, const void *d_tmpl, float *d_plane,
+                          size_t ld, fdas_stream_t stream) {
+    fdas_status st = fdas_check_params(p);
+    if (st != FDAS_OK) return st;
+    if ((st = check_shape(p, n, ld)) != FDAS_OK) return st;
+    if (!d_spec || !d_tmpl || !d_plane) return FDAS_ERR_INVALID_ARG;
+    if (!aligned16(d_spec) || !aligned16(d_tmpl) || !aligned16(d_plane)) return FDAS_ERR_INVALID_ARG;
+    const Geometry g = fdas::geometry(*p);
+    return cuda_status(fdas::launch_convolve_fp32(g, static_cast<const float2 *>(d_spec), n,
+                                                  static_cast<const float2 *>(d_tmpl), d_plane, ld, stream));
+}
+
+fdas_status fdas_harmonic_sum(const fdas_params *p, const float *d_plane, size_t n, size_t ld, const float *d_thresh,
+                              fdas_cand *d_cands, uint32_t *d_counts, fdas_cand *d_peaks, void *d_ws, size_t ws_bytes,
+                              fdas_stream_t stream) {
+    fdas_status st = fdas_check_params(p);
+    if (st != FDAS_OK) return st;
+    if ((st = check_shape(p, n, ld)) != FDAS_OK) return st;
+    if (!d_plane || !d_thresh || !d_cands || !d_counts || !d_ws) return FDAS_ERR_INVALID_ARG;
+    if (!aligned16(d_plane) || !aligned16(d_ws) || ((uintptr_t)d_thresh & 3u) || ((uintptr_t)d_cands & 3u) ||
+        ((uintptr_t)d_counts & 3u) || ((uintptr_t)d_peaks & 3u))
+        return FDAS_ERR_INVALID_ARG;
+    if (ws_bytes < fdas_workspace_bytes(p, n)) return FDAS_ERR_WORKSPACE;
+    const fdas::HsWorkspace ws = fdas::hs_workspace(d_ws, p->n_harm);
+    return cuda_status(
+        fdas::launch_harmonic(*p, d_plane, n, ld, d_thresh, d_cands, d_counts, d_peaks, ws, stream));
+}
+
+fdas_status fdas_search(const fdas_params *p, const void *d_spec, size_t n, const void *d_tmpl, float *d_plane,
+                        size_t ld, const float *d_thresh, fdas_cand *d_cands, uint32_t *d_counts, fdas_cand *d_peaks,
+                        void *d_ws, size_t ws_bytes, fdas_stream_t stream) {
+    // Check everything before enqueueing anything.
+    fdas_status st = fdas_check_params(p);
+    if (st != FDAS_OK) return st;
+    if ((st = check_shape(p, n, ld)) != FDAS_OK) return st;
+    if (!d_spec || !d_tmpl || !d_plane || !d_thresh || !d_cands || !d_counts || !d_ws) return FDAS_ERR_INVALID_ARG;
+    if (!aligned16(d_spec) || !aligned16(d_tmpl) || !aligned16(d_plane) || !aligned16(d_ws)) return FDAS_ERR_INVALID_ARG;
+    if (((uintptr_t)d_thresh & 3u) || ((uintptr_t)d_cands & 3u) || ((uintptr_t)d_counts & 3u) ||
+        ((uintptr_t)d_peaks & 3u))
+        return FDAS_ERR_INVALID_ARG;
+    if (ws_bytes < fdas_workspace_bytes(p, n)) return FDAS_ERR_WORKSPACE;
+    st = fdas_convolve(p, d_spec, n, d_tmpl, d_plane, ld, stream);
+    if (st != FDAS_OK) return st;
+    return fdas_harmonic_sum(p, d_plane, n, ld, d_thresh, d_cands, d_counts, d_peaks, d_ws, ws_bytes, stream);
+}
+
+fdas_status fdas_search_host(const fdas_params *p, const void *h_spec, size_t n, void *d_spec, const void *d_tmpl,
+                             float *d_plane, size_t ld, const float *d_thresh, fdas_cand *d_cands, uint32_t *d_counts,
+                             fdas_cand *d_peaks, fdas_cand *h_cands, uint32_t *h_counts, fdas_cand *h_peaks,
+                             void *d_ws, size_t ws_bytes, fdas_stream_t stream) {
+    fdas_status st = fdas_check_params(p);
+    if (st != FDAS_OK) return st;
+    if (!h_spec || !h_cands || !h_counts || (h_peaks && !d_peaks)) return FDAS_ERR_INVALID_ARG;
+    if ((st = check_shape(p, n, ld)) != FDAS_OK) return st;
+    if (!d_spec || !aligned16(d_spec)) return FDAS_ERR_INVALID_ARG;
+    cudaError_t e = cudaMemcpyAsync(d_spec, h_spec, n * 8u, cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) return FDAS_ERR_CUDA;
+    st = fdas_search(p, d_spec, n, d_tmpl, d_plane, ld, d_thresh, d_cands, d_counts, d_peaks, d_ws, ws_bytes, stream);
+    if (st != FDAS_OK) return st;
+    const size_t cand_bytes = (size_t)p->n_harm * p->cand_cap * sizeof(fdas_cand);
+    if ((e = cudaMemcpyAsync(h_cands, d_cands, cand_bytes, cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
+        return FDAS_ERR_CUDA;
+    if ((e = cudaMemcpyAsync(h_counts, d_counts, p->n_harm * sizeof(uint32_t), cudaMemcpyDeviceToHost, stream)) !=
+        cudaSuccess)
+        return FDAS_ERR_CUDA;
+    if (h_peaks && (e = cudaMemcpyAsync(h_peaks, d_peaks, p->n_harm * sizeof(fdas_cand), cudaMemcpyDeviceToHost,
+                                        stream)) != cudaSuccess)
+        return FDAS_ERR_CUDA;
+    return cuda_status(cudaStreamSynchronize(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,230 @@
+// FT convolution by overlap-save with fused power and discard (Sec. 2.1: OLS-FDFIR, AOLS-2048-P).
+//
+// For template t the plane row is P[t][j] = |sum_q X[j+q] conj(a_t[q])|^2. Overlap-save computes it
+// per segment s of F = 2048 input points, w_s[n] = X[s*L - h + n] (zero outside [0, N)), as
+//     u = IDFT(DFT(w_s) * T_t),   P[t][s*L + m] = |u[h + m]|^2,  m = 0..L-1,  L = F - n_tap + 1,
+// where T_t = conj(DFT(wrapped taps)) comes from fdas_make_templates. As in the paper's AOLS
+// kernel, the segment is transformed once and reused for every template. The F - L wrapped
+// outputs are never stored, which fuses the "discard" of the FOP preparation (Sec. 3.2).
+//
+// GB300 mapping: one CTA of 128 threads owns one segment (and a range of templates). Each thread
+// holds 16 complex points in registers. A 2048-point FFT is three Stockham passes, radix
+// 16 x 16 x 8, with two shared-memory exchanges in a padded layout that is conflict-free for
+// 64-bit accesses. After the forward FFT, thread tid holds frequency m = tid + 128 q in register
+// q. This is exactly the input layout of the inverse FFT's first pass, so the product with the
+// template needs no exchange. The template values are read from global memory (the 1.4 MB bank
+// stays in L2) with coalesced 8-byte loads. After the inverse FFT, thread tid holds time index
+// n = tid + 128 q, so the power stores of a warp are 32 consecutive columns.
+#include "fdas_internal.cuh"
+
+namespace fdas {
+namespace {
+
+constexpr int kF = 2048;
+constexpr int kThreads = 128;
+constexpr int kPadded = kF + kF / 16;  // one pad element after every 16
+
+__device__ __forceinline__ int pad(int e) { return e + (e >> 4); }
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cmul_conj(float2 a, float2 b) {  // a * conj(b)
+    return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+template <bool INV>
+__device__ __forceinline__ float2 twiddle(float2 v, float2 w) {  // w = exp(-2 pi i x); INV uses conj(w)
+    return INV ? cmul_conj(v, w) : cmul(v, w);
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+
+// In-place 4-point DFT of (a, b, c, d) with sign exp(-+2 pi i / 4); outputs in natural order.
+template <bool INV>
+__device__ __forceinline__ void dft4(float2 &a, float2 &b, float2 &c, float2 &d) {
+    const float2 s0 = cadd(a, c), s1 = csub(a, c), s2 = cadd(b, d), s3 = csub(b, d);
+    a = cadd(s0, s2);
+    c = csub(s0, s2);
+    if (!INV) {
+        b = make_float2(s1.x + s3.y, s1.y - s3.x);  // s1 - i s3
+        d = make_float2(s1.x - s3.y, s1.y + s3.x);  // s1 + i s3
+    } else {
+        b = make_float2(s1.x - s3.y, s1.y + s3.x);
+        d = make_float2(s1.x + s3.y, s1.y - s3.x);
+    }
+}
+
+// Multiply by exp(-+2 pi i m / 16) for the constant m (0 < m < 16).
+template <bool INV, int M>
+__device__ __forceinline__ float2 w16(float2 v) {
+    constexpr float c1 = 0.92387953251128674f, s1 = 0.38268343236508977f, r = 0.70710678118654752f;
+    constexpr int m = M & 15;
+    constexpr float wr = m == 0 ? 1.f : m == 1 ? c1 : m == 2 ? r : m == 3 ? s1 : m == 4 ? 0.f : m == 5 ? -s1
+                       : m == 6 ? -r : m == 7 ? -c1 : m == 8 ? -1.f : m == 9 ? -c1 : m == 10 ? -r : m == 11 ? -s1
+                       : m == 12 ? 0.f : m == 13 ? s1 : m == 14 ? r : c1;
+    constexpr float wi0 = m == 0 ? 0.f : m == 1 ? -s1 : m == 2 ? -r : m == 3 ? -c1 : m == 4 ? -1.f : m == 5 ? -c1
+                        : m == 6 ? -r : m == 7 ? -s1 : m == 8 ? 0.f : m == 9 ? s1 : m == 10 ? r : m == 11 ? c1
+                        : m == 12 ? 1.f : m == 13 ? c1 : m == 14 ? r : s1;
+    constexpr float wi = INV ? -wi0 : wi0;
+    if (m == 4) return INV ? make_float2(-v.y, v.x) : make_float2(v.y, -v.x);
+    return make_float2(fmaf(v.x, wr, -v.y * wi), fmaf(v.x, wi, v.y * wr));
+}
+
+// 16-point DFT in registers, natural order in and out: radix 4 x 4 with internal twiddles.
+template <bool INV>
+__device__ __forceinline__ void dft16(float2 (&v)[16]) {
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) dft4<INV>(v[n2], v[4 + n2], v[8 + n2], v[12 + n2]);
+    // v[4 k1 + n2] *= W16^(n2 k1)
+    v[5] = w16<INV, 1>(v[5]);
+    v[6] = w16<INV, 2>(v[6]);
+    v[7] = w16<INV, 3>(v[7]);
+    v[9] = w16<INV, 2>(v[9]);
+    v[10] = w16<INV, 4>(v[10]);
+    v[11] = w16<INV, 6>(v[11]);
+    v[13] = w16<INV, 3>(v[13]);
+    v[14] = w16<INV, 6>(v[14]);
+    v[15] = w16<INV, 9>(v[15]);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) dft4<INV>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+    // v[4 k1 + k2] holds X[k1 + 4 k2]: transpose the 4 x 4 register block.
+    float2 t[16];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) t[k1 + 4 * k2] = v[4 * k1 + k2];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = t[i];
+}
+
+// 8-point DFT in registers, natural order in and out: radix 4 x 2.
+template <bool INV>
+__device__ __forceinline__ void dft8(float2 (&v)[8]) {
+    dft4<INV>(v[0], v[2], v[4], v[6]);
+    dft4<INV>(v[1], v[3], v[5], v[7]);
+    v[3] = w16<INV, 2>(v[3]);  // W8^1
+    v[5] = w16<INV, 4>(v[5]);  // W8^2
+    v[7] = w16<INV, 6>(v[7]);  // W8^3
+    float2 t[8];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+        t[k1] = cadd(v[2 * k1], v[2 * k1 + 1]);
+        t[k1 + 4] = csub(v[2 * k1], v[2 * k1 + 1]);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = t[i];
+}
+
+// Passes 1 and 2 of the Stockham FFT: registers (A[tid + 128 r]) -> pass 1 -> buf0 -> pass 2 -> buf1.
+template <bool INV>
+__device__ __forceinline__ void fft_passes_12(float2 (&v)[16], float2 *buf0, float2 *buf1, const float2 (&tw2)[16],
+                                              int tid) {
+    dft16<INV>(v);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) buf0[pad(16 * tid + r)] = v[r];
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = buf0[pad(tid + 128 * r)];
+#pragma unroll
+    for (int r = 1; r < 16; ++r) v[r] = twiddle<INV>(v[r], tw2[r]);
+    dft16<INV>(v);
+    const int base = (tid >> 4) * 256 + (tid & 15);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) buf1[pad(base + 16 * r)] = v[r];
+    __syncthreads();
+}
+
+// Pass 3 for butterfly b = tid + 128 hh: reads buf1[b + 256 r], returns index b + 256 r in u[r].
+template <bool INV>
+__device__ __forceinline__ void fft_pass_3(float2 (&u)[8], const float2 *buf1, const float2 (&tw3)[8], int b) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) u[r] = buf1[pad(b + 256 * r)];
+#pragma unroll
+    for (int r = 1; r < 8; ++r) u[r] = twiddle<INV>(u[r], tw3[r]);
+    dft8<INV>(u);
+}
+
+__global__ void __launch_bounds__(kThreads, 3)
+    fdas_ols_fp32(const float2 *__restrict__ spec, int n, const float2 *__restrict__ tmpl, int n_temp, int h, int keep,
+                  float *__restrict__ plane, size_t ld, int n_seg, int t_chunk, int n_tchunk) {
+    __shared__ float2 buf0[kPadded];
+    __shared__ float2 buf1[kPadded];
+    const int tid = threadIdx.x;
+    const float2 *wtab = tmpl + (size_t)n_temp * kF;  // exp(-2 pi i k / F)
+
+    // Stockham twiddles of this thread, fixed for the whole kernel.
+    float2 tw2[16], tw3a[8], tw3b[8];
+    {
+        const int k = tid & 15;
+#pragma unroll
+        for (int r = 0; r < 16; ++r) tw2[r] = __ldg(&wtab[8 * ((k * r) & 255)]);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            tw3a[r] = __ldg(&wtab[tid * r]);
+            tw3b[r] = __ldg(&wtab[(tid + 128) * r]);
+        }
+    }
+    const float scale = 1.0f / kF;
+    const int n_items = n_seg * n_tchunk;
+
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int s = item / n_tchunk;
+        const int t0 = (item - s * n_tchunk) * t_chunk;
+        const int t1 = min(t0 + t_chunk, n_temp);
+        const int origin = s * keep - h;  // input index of segment point 0
+
+        // Forward FFT of the segment: W[q] = DFT(w_s)[tid + 128 q] / F.
+        float2 v[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+            const int idx = origin + tid + 128 * r;
+            v[r] = (idx >= 0 && idx < n) ? __ldg(&spec[idx]) : make_float2(0.f, 0.f);
+        }
+        fft_passes_12<false>(v, buf0, buf1, tw2, tid);
+        float2 W[16];
+        {
+            float2 u[8];
+            fft_pass_3<false>(u, buf1, tw3a, tid);
+#pragma unroll
+            for (int r = 0; r < 8; ++r) W[2 * r] = make_float2(u[r].x * scale, u[r].y * scale);
+            fft_pass_3<false>(u, buf1, tw3b, tid + 128);
+#pragma unroll
+            for (int r = 0; r < 8; ++r) W[2 * r + 1] = make_float2(u[r].x * scale, u[r].y * scale);
+        }
+
+        for (int t = t0; t < t1; ++t) {
+            const float2 *T = tmpl + (size_t)t * kF + tid;
+#pragma unroll
+            for (int q = 0; q < 16; ++q) v[q] = cmul(W[q], __ldg(&T[128 * q]));
+            fft_passes_12<true>(v, buf0, buf1, tw2, tid);
+            float *row = plane + (size_t)t * ld;
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                float2 u[8];
+                const int b = tid + 128 * hh;
+                fft_pass_3<true>(u, buf1, hh ? tw3b : tw3a, b);
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    const int m = b + 256 * r;  // time index within the segment
+                    const int col = s * keep + m - h;
+                    if (m >= h && m < h + keep && col < n) row[col] = fmaf(u[r].x, u[r].x, u[r].y * u[r].y);
+                }
+            }
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_convolve_fp32(const Geometry &g, const float2 *spec, size_t n, const float2 *tmpl, float *plane,
+                                 size_t ld, cudaStream_t s) {
+    const int n_seg = (int)((n + g.keep - 1) / g.keep);
+    const int t_chunk = g.n_temp;  // one work item per segment: forward FFT once, all templates
+    const int n_tchunk = (g.n_temp + t_chunk - 1) / t_chunk;
+    const int n_items = n_seg * n_tchunk;
+    fdas_ols_fp32<<<n_items, kThreads, 0, s>>>(spec, (int)n, tmpl, g.n_temp, g.h, g.keep, plane, ld, n_seg, t_chunk,
+                                                n_tchunk);
+    return cudaGetLastError();
+}
+
+}  // namespace fdas

@@ -1,0 +1,58 @@
+// Internal declarations shared by the FDAS CUDA translation units (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/fdas.h"
+
+namespace fdas {
+
+// Derived sizes of one parameter set.
+struct Geometry {
+    int n_temp;   // template rows
+    int c;        // centre row (zero drift), (n_temp-1)/2
+    int n_tap;    // taps per template
+    int h;        // half width, (n_tap-1)/2
+    int fft_len;  // overlap-save segment length F
+    int keep;     // valid outputs per segment, L = F - n_tap + 1
+};
+
+inline Geometry geometry(const fdas_params &p) {
+    Geometry g;
+    g.n_temp = p.n_temp;
+    g.c = (p.n_temp - 1) / 2;
+    g.n_tap = p.n_tap;
+    g.h = (p.n_tap - 1) / 2;
+    g.fft_len = p.fft_len;
+    g.keep = p.fft_len - p.n_tap + 1;
+    return g;
+}
+
+// Workspace layout of the harmonic-sum stage (all 8-byte words):
+//   [0, n_harm)                 raw crossing counters (low 32 bits used)
+//   [n_harm, 2 n_harm)          peak keys, one per plane
+//   [4 n_harm, 4 n_harm + n_harm*FDAS_RAW_CAP)  raw candidate keys, FDAS_RAW_CAP per plane
+struct HsWorkspace {
+    unsigned long long *counters;
+    unsigned long long *peaks;
+    unsigned long long *raw;
+};
+
+inline HsWorkspace hs_workspace(void *ws, int n_harm) {
+    unsigned long long *w = static_cast<unsigned long long *>(ws);
+    return HsWorkspace{w, w + n_harm, w + 4 * n_harm};
+}
+
+inline size_t hs_workspace_words(int n_harm) { return (size_t)n_harm * (FDAS_RAW_CAP + 4); }
+
+// Kernel launchers (each returns cudaGetLastError() of its launch).
+cudaError_t launch_templates(const fdas_params &p, void *d_tmpl, cudaStream_t s);
+cudaError_t launch_convolve_fp32(const Geometry &g, const float2 *spec, size_t n, const float2 *tmpl,
+                                 float *plane, size_t ld, cudaStream_t s);
+cudaError_t launch_harmonic(const fdas_params &p, const float *plane, size_t n, size_t ld,
+                            const float *thresh, fdas_cand *cands, uint32_t *counts, fdas_cand *peaks,
+                            const HsWorkspace &ws, cudaStream_t s);
+
+}  // namespace fdas

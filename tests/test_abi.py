@@ -1,0 +1,124 @@
+"""The C ABI library loads, exports every symbol include/fdas.h declares, and checks its
+arguments on the host (CPU only: no call here reaches a kernel)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "fdas.h")
+
+
+@pytest.fixture(scope="module")
+def fd():
+    from paper_1806_01556_gb300 import build
+
+    build.build()
+    import paper_1806_01556_gb300 as fdas
+
+    fdas.lib()
+    return fdas
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fdas_[a-z_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported_and_bound(fd):
+    from paper_1806_01556_gb300 import _lib
+
+    names = declared_functions()
+    assert len(names) >= 12
+    lib = fd.lib()
+    for name in names:
+        assert hasattr(lib, name), name
+        assert name in _lib.SIGNATURES, f"{name} has no ctypes signature"
+    assert set(_lib.SIGNATURES) == set(names)
+
+
+def test_struct_layouts_match_header(fd):
+    from paper_1806_01556_gb300 import _lib
+
+    assert C.sizeof(_lib.fdas_params) == 36
+    assert C.sizeof(_lib.fdas_cand) == 12
+    assert fd.CAND_DTYPE.itemsize == 12
+
+
+def test_defaults_and_sizes(fd):
+    from paper_1806_01556_gb300 import _lib
+
+    p = _lib.fdas_params()
+    fd.lib().fdas_default_params(C.byref(p))
+    assert (p.n_temp, p.z_min, p.z_step, p.n_tap, p.fft_len, p.n_harm, p.harm_mask, p.cand_cap) == (
+        85, -42, 1, 421, 2048, 8, 0xFF, 200)
+    q = fd.Params()
+    assert fd.fdas_check_params(q) == 0
+    assert fd.fdas_templates_bytes(q) == 86 * 2048 * 8
+    assert fd.fdas_plane_bytes(q, 1 << 21, 1 << 21) == 85 * (1 << 21) * 4
+    assert fd.fdas_workspace_bytes(q, 1 << 21) == 8 * 8 * (16384 + 4)
+
+
+@pytest.mark.parametrize(
+    "change,code",
+    [
+        (dict(n_temp=84), -1),
+        (dict(n_temp=1, z_min=0), -1),
+        (dict(z_min=-41), -1),
+        (dict(n_tap=420), -1),
+        (dict(n_tap=1025), -1),
+        (dict(fft_len=3000), -1),
+        (dict(n_harm=17), -1),
+        (dict(harm_mask=0), -1),
+        (dict(harm_mask=0x100), -1),
+        (dict(cand_cap=0), -1),
+        (dict(cand_cap=5000), -1),
+        (dict(precision=7), -1),
+        (dict(fft_len=4096), -2),
+        (dict(precision=1), -2),
+        (dict(n_temp=9, z_min=-8, z_step=2), 0),
+        (dict(n_harm=16, harm_mask=0xFFFF), 0),
+    ],
+)
+def test_param_validation(fd, change, code):
+    p = fd.Params(**change)
+    assert fd.fdas_check_params(p) == code
+
+
+def test_thresholds_match_oracle(fd):
+    from oracle import thresholds
+
+    for kind, name in ((0, "gamma"), (1, "meansd")):
+        for sigma in (6.0, 3.0):
+            p = fd.Params(n_harm=16, harm_mask=0xFFFF)
+            got = fd.fdas_default_thresholds(p, sigma, kind)
+            want = thresholds.threshold_array(16, 85, sigma=sigma, kind=name)
+            assert np.all(np.abs(got.view(np.int32) - want.view(np.int32)) <= 1)
+
+
+def test_bad_pointers_are_rejected_before_any_launch(fd):
+    lib = fd.lib()
+    p = fd.Params().c()
+    null = C.c_void_p(0)
+    fake = C.c_void_p(0x10000)  # never dereferenced: argument checks fail first
+    odd = C.c_void_p(0x10004)
+    assert lib.fdas_make_templates(C.byref(p), null, null) == -1
+    assert lib.fdas_make_templates(C.byref(p), odd, null) == -1
+    assert lib.fdas_convolve(C.byref(p), null, 100, fake, fake, 100, null) == -1
+    assert lib.fdas_convolve(C.byref(p), fake, 0, fake, fake, 100, null) == -1
+    assert lib.fdas_convolve(C.byref(p), fake, 100, fake, fake, 99, null) == -1
+    assert lib.fdas_convolve(C.byref(p), fake, (1 << 24) + 1, fake, fake, 1 << 25, null) == -1
+    assert lib.fdas_convolve(C.byref(p), odd, 100, fake, fake, 100, null) == -1
+    ws = fd.fdas_workspace_bytes(fd.Params(), 100)
+    assert lib.fdas_harmonic_sum(C.byref(p), fake, 100, 100, fake, fake, fake, null, fake, ws - 8, null) == -3
+    assert lib.fdas_harmonic_sum(C.byref(p), fake, 100, 100, null, fake, fake, null, fake, ws, null) == -1
+    assert lib.fdas_search(C.byref(p), fake, 100, fake, fake, 100, fake, fake, fake, null, fake, 16, null) == -3
+    bad = fd.Params(fft_len=4096).c()
+    assert lib.fdas_search(C.byref(bad), fake, 100, fake, fake, 100, fake, fake, fake, null, fake, ws, null) == -2
+    assert lib.fdas_search_host(C.byref(p), null, 100, fake, fake, fake, 100, fake, fake, fake, null, fake, fake,
+                                null, fake, ws, null) == -1
+    assert lib.fdas_default_thresholds(C.byref(p), 6.0, 2, fake) == -1
+    assert lib.fdas_status_string(-3) == b"workspace too small"

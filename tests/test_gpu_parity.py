@@ -1,0 +1,291 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances:
+* Template bank: max |T_gpu - T_ref| <= 1e-6 * max |T_ref| (one float32 rounding of FP64 values).
+* F-A plane: rel = |P_gpu - P_ref| / max(P_ref, mean P_ref) <= 1e-4, the bar for the float32 path.
+  The max and RMS are printed for every case.
+* Harmonic sum fed the oracle's float32 plane: candidates, counts and peaks bit for bit.
+"""
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import correlate, harmonic, templates, thresholds
+
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-4
+
+
+def plane_rel(gpu, ref):
+    rel = np.abs(gpu.astype(np.float64) - ref) / np.maximum(ref, ref.mean())
+    return rel.max(), np.sqrt(np.mean(rel**2))
+
+
+def run_convolve(fd, p, spec, ld=None, fill=np.nan):
+    n = len(spec)
+    ld = n if ld is None else ld
+    tmpl = torch.empty(fd.fdas_templates_bytes(p), dtype=torch.uint8, device="cuda")
+    fd.fdas_make_templates(p, tmpl)
+    d_spec = torch.from_numpy(np.ascontiguousarray(spec, dtype=np.complex64)).cuda()
+    plane = torch.full((p.n_temp, ld), fill, dtype=torch.float32, device="cuda")
+    fd.fdas_convolve(p, d_spec, n, tmpl, plane, ld)
+    torch.cuda.synchronize()
+    return plane.cpu().numpy(), tmpl
+
+
+def run_harmonic(fd, p, plane32, thresh, ld=None):
+    n_temp, n = plane32.shape
+    ld = n if ld is None else ld
+    d_plane = torch.full((n_temp, ld), 1e30, dtype=torch.float32, device="cuda")
+    d_plane[:, :n] = torch.from_numpy(np.ascontiguousarray(plane32)).cuda()
+    d_ta = torch.from_numpy(np.ascontiguousarray(thresh, dtype=np.float32)).cuda()
+    ws_bytes = fd.fdas_workspace_bytes(p, n)
+    ws = torch.full((ws_bytes,), 0xAB, dtype=torch.uint8, device="cuda")  # contents need no initialisation
+    cands = torch.zeros(p.n_harm * p.cand_cap * 12, dtype=torch.uint8, device="cuda")
+    counts = torch.zeros(p.n_harm, dtype=torch.int32, device="cuda")
+    peaks = torch.zeros(p.n_harm * 12, dtype=torch.uint8, device="cuda")
+    fd.fdas_harmonic_sum(p, d_plane, n, ld, d_ta, cands, counts, peaks, ws, ws_bytes)
+    torch.cuda.synchronize()
+    counts = counts.cpu().numpy().astype(np.uint32)
+    return fd.decode_cands(cands.cpu().numpy(), counts, p.cand_cap), counts, peaks.cpu().numpy().view(fd.CAND_DTYPE)
+
+
+def assert_same_candidates(got_cands, got_counts, got_peaks, ref, mask):
+    assert [int(c) for c in got_counts] == [int(c) for c in ref.counts]
+    for k, (g, r) in enumerate(zip(got_cands, ref.cands), start=1):
+        assert len(g) == len(r), k
+        assert np.array_equal(g["power"].view(np.uint32), r["power"].view(np.uint32)), k
+        assert np.array_equal(g["i"], r["i"]) and np.array_equal(g["j"], r["j"]), k
+        assert np.all(g["k"] == k)
+    for k, (g, r) in enumerate(zip(got_peaks, ref.peaks), start=1):
+        assert (np.float32(g["power"]).view(np.uint32), int(g["i"]), int(g["j"])) == (
+            np.float32(r[0]).view(np.uint32), r[1], r[2]), k
+
+
+# ---------------------------------------------------------------- templates
+
+
+@pytest.mark.parametrize(
+    "kw", [dict(), dict(n_temp=9, z_min=-8, z_step=2, n_tap=101), dict(n_temp=3, z_min=-1, n_tap=1023)]
+)
+def test_templates_match_oracle(fd, kw):
+    p = fd.Params(**kw)
+    grid = templates.TemplateGrid(p.n_temp, float(p.z_min), float(p.z_step), p.n_tap)
+    ref = templates.frequency_templates(templates.template_bank(grid), p.fft_len)
+    tmpl = torch.empty(fd.fdas_templates_bytes(p), dtype=torch.uint8, device="cuda")
+    fd.fdas_make_templates(p, tmpl)
+    torch.cuda.synchronize()
+    got = tmpl.cpu().numpy().view(np.complex64).reshape(p.n_temp + 1, p.fft_len)
+    err = np.max(np.abs(got[: p.n_temp] - ref))
+    print(f"templates {kw}: max abs err {err:.3e} (max |T| {np.max(np.abs(ref)):.3f})")
+    assert err <= 1e-6 * np.max(np.abs(ref))
+    twiddle = np.exp(-2j * np.pi * np.arange(p.fft_len) / p.fft_len)
+    assert np.max(np.abs(got[p.n_temp] - twiddle)) < 1.2e-7
+
+
+# ---------------------------------------------------------------- convolution
+
+
+@pytest.mark.parametrize("n", [1, 2, 211, 1628, 1629, 3257, 5000, 20000])
+def test_plane_small_and_ragged(fd, bank, n):
+    p = fd.Params()
+    rng = np.random.default_rng(n)
+    spec = synth.complex_noise(rng, n) + synth.tone_spectrum(n, [synth.Tone(n // 2, 11, 15.0, 1)])
+    spec = spec.astype(np.complex64)
+    got, _ = run_convolve(fd, p, spec)
+    ref = correlate.plane_direct(spec, bank)
+    mx, rms = plane_rel(got, ref)
+    print(f"N={n}: plane rel max {mx:.2e} rms {rms:.2e}")
+    assert mx <= REL_TOL
+
+
+def test_plane_leaves_padding_columns_untouched(fd, bank):
+    p = fd.Params()
+    n, ld = 3000, 3072
+    spec = synth.complex_noise(np.random.default_rng(2), n).astype(np.complex64)
+    got, _ = run_convolve(fd, p, spec, ld=ld, fill=-7.0)
+    assert np.all(got[:, n:] == -7.0)
+    mx, _ = plane_rel(got[:, :n], correlate.plane_direct(spec, bank))
+    assert mx <= REL_TOL
+
+
+def test_plane_small_workload(fd, small_case):
+    wl, ref = small_case
+    got, _ = run_convolve(fd, fd.Params(), wl.spectrum)
+    mx, rms = plane_rel(got, ref)
+    print(f"N=2^16 small workload: plane rel max {mx:.2e} rms {rms:.2e}, max|dP|/maxP "
+          f"{np.max(np.abs(got - ref)) / ref.max():.2e}")
+    assert mx <= REL_TOL
+    assert np.unravel_index(np.argmax(got), got.shape) == (62, 12000)
+    # zero-drift row is |X|^2 up to float32 FFT rounding
+    x = wl.spectrum.astype(np.complex128)
+    assert np.max(np.abs(got[42] - np.abs(x) ** 2) / np.maximum(np.abs(x) ** 2, 1.0)) < 1e-5
+
+
+def test_plane_other_template_grid(fd):
+    p = fd.Params(n_temp=9, z_min=-8, z_step=2, n_tap=101)
+    grid = templates.TemplateGrid(9, -8.0, 2.0, 101)
+    bank = templates.template_bank(grid)
+    n = 9000
+    spec = synth.complex_noise(np.random.default_rng(5), n).astype(np.complex64)
+    got, _ = run_convolve(fd, p, spec)
+    mx, _ = plane_rel(got, correlate.plane_ols(spec, bank, 2048))
+    assert mx <= REL_TOL
+
+
+def test_plane_full_size(fd, ska_case):
+    """N = 2^21, 85 templates: the whole plane against the oracle, in the bench's launch configuration."""
+    wl, ref = ska_case
+    p = fd.Params()
+    s = fd.Searcher(p, wl.n)
+    d_spec = torch.from_numpy(wl.spectrum).cuda()
+    s.search(d_spec, wl.n)
+    torch.cuda.synchronize()
+    got = s.plane[:, : wl.n].cpu().numpy()
+    mx, rms = plane_rel(got, ref)
+    print(f"N=2^21: plane rel max {mx:.2e} rms {rms:.2e}")
+    assert mx <= REL_TOL
+    # Spot points from the direct definition too (independent of the oracle's overlap-save route).
+    rng = np.random.default_rng(9)
+    rows = rng.integers(0, 85, 64)
+    cols = np.concatenate([rng.integers(0, wl.n, 56), [0, 1, 1627, 1628, wl.n - 2, wl.n - 1, 1628 * 1288, 2047]])
+    direct = correlate.power_at(wl.spectrum, templates.template_bank(), rows, cols)
+    rel = np.abs(got[rows, cols] - direct) / np.maximum(direct, 1.0)
+    assert rel.max() <= REL_TOL
+    # Every injected fundamental with |z| <= 42 peaks in its own row and column.
+    for t in wl.tones:
+        row = 42 + int(t.z)
+        col = int(t.mean_bin)
+        assert got[row, col] == got[row, col - 3 : col + 4].max()
+
+
+# ---------------------------------------------------------------- harmonic sum
+
+
+@pytest.mark.parametrize(
+    "kw,sigma",
+    [
+        (dict(n_harm=8, harm_mask=0b10001011), 6.0),
+        (dict(n_harm=8, harm_mask=0xFF), 3.0),
+        (dict(n_harm=16, harm_mask=0xFFFF, cand_cap=50), 3.5),
+        (dict(n_harm=4, harm_mask=0b0101, cand_cap=1), 2.5),
+    ],
+)
+def test_harmonic_bit_exact_small(fd, small_case, kw, sigma):
+    wl, ref_plane = small_case
+    p = fd.Params(**kw)
+    plane32 = ref_plane.astype(np.float32)
+    ta = thresholds.threshold_array(p.n_harm, 85, sigma=sigma)
+    got = run_harmonic(fd, p, plane32, ta)
+    ref = harmonic.detect(plane32, ta, p.n_harm, p.harm_mask, p.cand_cap)
+    print(f"{kw} sigma {sigma}: counts {list(ref.counts)}")
+    assert_same_candidates(*got, ref, p.harm_mask)
+
+
+@pytest.mark.parametrize("n,ld", [(1, 1), (7, 16), (1000, 1000), (4099, 4160)])
+def test_harmonic_bit_exact_edges(fd, n, ld):
+    p = fd.Params(n_temp=17, z_min=-8, n_harm=8, harm_mask=0xFF, cand_cap=64)
+    plane = synth.exponential_plane(np.random.default_rng(n), 17, n)
+    ta = thresholds.threshold_array(8, 17, sigma=1.5)
+    got = run_harmonic(fd, p, plane, ta, ld=ld)
+    ref = harmonic.detect(plane, ta, 8, 0xFF, 64)
+    assert_same_candidates(*got, ref, 0xFF)
+
+
+def test_harmonic_many_crossings_top_cap(fd):
+    # Hundreds to thousands of crossings per plane, all above cand_cap: the top 200 must be exact.
+    p = fd.Params()
+    plane = synth.exponential_plane(np.random.default_rng(21), 85, 1 << 15)
+    ta = np.concatenate(
+        [thresholds.threshold_array(8, 85, sigma=3.2 - 1.0 * k / 7)[k : k + 1] for k in range(8)]
+    )
+    got = run_harmonic(fd, p, plane, ta)
+    ref = harmonic.detect(plane, ta, 8, 0xFF, 200)
+    assert min(ref.counts) > 200 and max(ref.counts) < 16384, ref.counts
+    assert_same_candidates(*got, ref, 0xFF)
+
+
+def test_harmonic_raw_overflow_counts_everything(fd):
+    # More crossings than the raw buffer holds: counts stay exact and every record is a true crossing.
+    p = fd.Params(n_harm=2, harm_mask=0b11)
+    plane = synth.exponential_plane(np.random.default_rng(22), 85, 1 << 15)
+    ta = thresholds.threshold_array(2, 85, sigma=1.0)
+    cands, counts, _ = run_harmonic(fd, p, plane, ta)
+    ref = harmonic.detect(plane, ta, 2, 0b11, 200)
+    assert [int(c) for c in counts] == [int(c) for c in ref.counts]
+    assert min(ref.counts) > 16384
+    hp = {(k, i): v for k, i, v in harmonic.harmonic_planes(plane, 2)}
+    for k, rec in enumerate(cands, start=1):
+        assert len(rec) == 200
+        assert np.all(np.diff(rec["power"]) <= 0)
+        for r in rec:
+            assert hp[(k, int(r["i"]))][int(r["j"])] == r["power"] > ta[k - 1, 42 + int(r["i"])]
+
+
+def test_harmonic_bit_exact_full_size(fd, ska_case):
+    """N = 2^21: the harmonic sum fed the oracle's float32 plane returns the oracle's candidates."""
+    wl, ref_plane = ska_case
+    p = fd.Params()
+    plane32 = ref_plane.astype(np.float32)
+    ta = thresholds.threshold_array(8, 85, sigma=6.0)
+    got = run_harmonic(fd, p, plane32, ta, ld=wl.n + 64)
+    ref = harmonic.detect(plane32, ta, 8, 0xFF, 200)
+    print(f"N=2^21 counts {list(ref.counts)}")
+    assert_same_candidates(*got, ref, 0xFF)
+    assert sum(ref.counts) > 0
+
+
+# ---------------------------------------------------------------- whole search
+
+
+def test_search_host_equals_device_and_repeats(fd, small_case):
+    wl, _ = small_case
+    p = fd.Params(harm_mask=0b10001011)
+    s = fd.Searcher(p, wl.n)
+    d_spec = torch.from_numpy(wl.spectrum).cuda()
+    s.search(d_spec, wl.n)
+    torch.cuda.synchronize()
+    a = s.results()
+    h_spec = torch.from_numpy(wl.spectrum).pin_memory()
+    for _ in range(2):
+        s.search_host(h_spec, wl.n)
+        b = s.results(host=True)
+        assert np.array_equal(a[1], b[1])
+        for x, y in zip(a[0], b[0]):
+            assert x.tobytes() == y.tobytes()
+        assert a[2].tobytes() == b[2].tobytes()
+    # the injected tone is the loudest HP_1 point, at (i = +20, j = 12000)
+    top = a[0][0][0]
+    assert (int(top["i"]), int(top["j"])) == (20, 12000)
+
+
+def test_search_candidates_match_oracle_within_tolerance(fd, small_case):
+    """fdas_search on the GPU plane against Algorithm 1 on the oracle plane.
+
+    Where they differ, the point must lie within the plane tolerance of the threshold.
+    """
+    wl, ref_plane = small_case
+    p = fd.Params(harm_mask=0b10001011)
+    ta = thresholds.threshold_array(8, 85, sigma=6.0)
+    s = fd.Searcher(p, wl.n, thresh=ta)
+    s.search(torch.from_numpy(wl.spectrum).cuda(), wl.n)
+    torch.cuda.synchronize()
+    cands, counts, _ = s.results()
+    ref32 = ref_plane.astype(np.float32)
+    ref = harmonic.detect(ref32, ta, 8, p.harm_mask, 200)
+    hp = {(k, i): v for k, i, v in harmonic.harmonic_planes(ref32, 8)}
+    tol = 2 * 8 * REL_TOL
+    for k in (1, 2, 4, 8):
+        assert counts[k - 1] < 200 and ref.counts[k - 1] < 200
+        g = {(int(r["i"]), int(r["j"])): float(r["power"]) for r in cands[k - 1]}
+        r = {(int(x["i"]), int(x["j"])): float(x["power"]) for x in ref.cands[k - 1]}
+        for q, v in g.items():
+            want = float(hp[(k, q[0])][q[1]])
+            assert abs(v - want) <= tol * want
+            if q not in r:
+                assert want >= ta[k - 1, 0] * (1 - tol)
+        for q in set(r) - set(g):
+            assert r[q] <= ta[k - 1, 0] * (1 + tol)
+    assert (int(cands[0][0]["i"]), int(cands[0][0]["j"])) == (20, 12000)
