@@ -128,6 +128,28 @@ def dist_env():
     return world, rank, local
 
 
+def rank_seed(rank: int) -> int:
+    """Each rank searches its own spectrum (an independent DM trial): seed 1 + rank."""
+    return 1 + rank
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """The slowest rank's time (all_reduce MAX); the identity on one rank."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, steps: int, seconds: float) -> float:
+    """Whole-job spectra/s: every rank processes `steps` spectra in the (max-over-ranks) time."""
+    return world * steps / seconds
+
+
 def cpu_oracle_sample(wl, sample_bins):
     """Time the FP64 oracle (overlap-save plane + Algorithm 1) on the first sample_bins bins.
 
@@ -156,7 +178,7 @@ def run_reference(args):
     import synth
 
     wl = synth.ska_workload(n=args.n, seed=1)
-    sample = min(args.n, 1 << 17)
+    sample = min(args.n, 1 << 16)
     for _ in range(args.warmup):
         cpu_oracle_sample(wl, sample)
     times = []
@@ -204,7 +226,7 @@ def run_fdas(args):
         torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    wl = synth.ska_workload(n=args.n, seed=1 + rank)
+    wl = synth.ska_workload(n=args.n, seed=rank_seed(rank))
     # The CPU baseline runs before any timed GPU work (rank 0, N = 1 only).
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -248,15 +270,11 @@ def run_fdas(args):
         end.record(stream)
         torch.cuda.synchronize(dev)
         barrier()
-    total_ms = start.elapsed_time(end)
+    total_ms = max_over_ranks(start.elapsed_time(end), world, dev)
     conv_ms = [e[0].elapsed_time(e[1]) for e in events]
     hs_ms = [e[1].elapsed_time(e[2]) for e in events]
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
     ms_per_step = total_ms / args.steps
-    value = world * args.steps / (total_ms / 1e3)
+    value = job_throughput(world, args.steps, total_ms / 1e3)
 
     # End to end through fdas_search_host: pinned host spectrum in, candidates out, every step.
     h_spec = torch.from_numpy(wl.spectrum).pin_memory()
@@ -266,11 +284,7 @@ def run_fdas(args):
     t0 = time.perf_counter()
     for _ in range(args.steps):
         s.search_host(h_spec, args.n)
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
     cands, counts, _ = s.results(host=True)
 
     if rank == 0:
@@ -301,7 +315,7 @@ def run_fdas(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(args.n),
             "fa_points_per_s": value * 85 * args.n,
             "clocks": sampler.summary(),
-            "e2e": {"value": world * args.steps / e2e_s, "unit": "spectra/s",
+            "e2e": {"value": job_throughput(world, args.steps, e2e_s), "unit": "spectra/s",
                     "h2d_bytes_per_step": args.n * 8, "d2h_bytes_per_step": d2h},
             "gpu_launches": 4 * args.steps,
             "roofline": roof,

@@ -170,7 +170,7 @@ def test_plane_full_size(fd, ska_case):
         (dict(n_harm=8, harm_mask=0b10001011), 6.0),
         (dict(n_harm=8, harm_mask=0xFF), 3.0),
         (dict(n_harm=16, harm_mask=0xFFFF, cand_cap=50), 3.5),
-        (dict(n_harm=4, harm_mask=0b0101, cand_cap=1), 2.5),
+        (dict(n_harm=4, harm_mask=0b0101, cand_cap=1), 3.0),
     ],
 )
 def test_harmonic_bit_exact_small(fd, small_case, kw, sigma):
