@@ -267,18 +267,18 @@ def test_search_candidates_match_oracle_within_tolerance(fd, small_case):
     Where they differ, the point must lie within the plane tolerance of the threshold.
     """
     wl, ref_plane = small_case
-    p = fd.Params(harm_mask=0b10001011)
+    p = fd.Params(harm_mask=0b10001011, cand_cap=1000)  # the tone's sidelobes give ~330 crossings
     ta = thresholds.threshold_array(8, 85, sigma=6.0)
     s = fd.Searcher(p, wl.n, thresh=ta)
     s.search(torch.from_numpy(wl.spectrum).cuda(), wl.n)
     torch.cuda.synchronize()
     cands, counts, _ = s.results()
     ref32 = ref_plane.astype(np.float32)
-    ref = harmonic.detect(ref32, ta, 8, p.harm_mask, 200)
+    ref = harmonic.detect(ref32, ta, 8, p.harm_mask, 1000)
     hp = {(k, i): v for k, i, v in harmonic.harmonic_planes(ref32, 8)}
     tol = 2 * 8 * REL_TOL
     for k in (1, 2, 4, 8):
-        assert counts[k - 1] < 200 and ref.counts[k - 1] < 200
+        assert counts[k - 1] < 1000 and ref.counts[k - 1] < 1000
         g = {(int(r["i"]), int(r["j"])): float(r["power"]) for r in cands[k - 1]}
         r = {(int(x["i"]), int(x["j"])): float(x["power"]) for x in ref.cands[k - 1]}
         for q, v in g.items():
