@@ -202,6 +202,35 @@ fdas_status fdas_search_host(const fdas_params *p, const void *h_spec, size_t n,
                              fdas_cand *h_cands, uint32_t *h_counts, fdas_cand *h_peaks, void *d_ws,
                              size_t ws_bytes, fdas_stream_t stream);
 
+/*
+ * Scratch size of fdas_harmonic_sum_noalloc: the workspace of 8 harmonic planes,
+ * 8 * 8 * (FDAS_RAW_CAP + 4) bytes (about 1 MiB).
+ */
+#define FDAS_NOALLOC_SCRATCH_BYTES ((size_t)8 * 8 * (FDAS_RAW_CAP + 4))
+
+/*
+ * fdas_harmonic_sum without a caller-provided workspace. The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory at all. Examples are a stage that is
+ * handed only its input and output buffers by the framework that owns the GPU, or a real-time
+ * loop that must never call cudaMalloc (which can synchronise the whole device).
+ *
+ * The scratch is a static device array of FDAS_NOALLOC_SCRATCH_BYTES inside libfdas. Every GPU
+ * that loads the library holds it until the process exits. The call allocates nothing: no
+ * cudaMalloc, no cudaFree, no allocating library routine. Arguments and results are as for
+ * fdas_harmonic_sum, which it calls with that array as d_ws.
+ *   - Parameter sets whose workspace exceeds the array (n_harm > 8) are rejected with
+ *     FDAS_ERR_WORKSPACE, before anything is enqueued.
+ *   - The first call on a device looks up the array's device address, with that device current.
+ *     Make that first call before any stream capture.
+ *   - All calls on a device share the one array, which keeps the last call's contents. Each call
+ *     clears the counters it needs before use. Calls that overlap on the GPU (on different
+ *     streams, or from different host threads) race on the array and must be serialised by the
+ *     caller.
+ */
+fdas_status fdas_harmonic_sum_noalloc(const fdas_params *p, const float *d_plane, size_t n, size_t ld,
+                                      const float *d_thresh, fdas_cand *d_cands, uint32_t *d_counts,
+                                      fdas_cand *d_peaks, fdas_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -33,6 +33,7 @@ __all__ = [
     "fdas_harmonic_sum",
     "fdas_search",
     "fdas_search_host",
+    "fdas_harmonic_sum_noalloc",
     "decode_cands",
     "Searcher",
 ]
@@ -156,6 +157,17 @@ def fdas_search_host(p: Params, h_spec, n, d_spec, d_tmpl, d_plane, ld, d_thresh
             ws_bytes, _stream(stream),
         ),
         "fdas_search_host",
+    )
+
+
+def fdas_harmonic_sum_noalloc(p: Params, d_plane, n, ld, d_thresh, d_cands, d_counts, d_peaks, stream=None):
+    """fdas_harmonic_sum with the library's static scratch array instead of a workspace (n_harm <= 8)."""
+    _check(
+        lib().fdas_harmonic_sum_noalloc(
+            C.byref(p.c()), _ptr(d_plane), n, ld, _ptr(d_thresh), _ptr(d_cands), _ptr(d_counts), _ptr(d_peaks),
+            _stream(stream),
+        ),
+        "fdas_harmonic_sum_noalloc",
     )
 
 

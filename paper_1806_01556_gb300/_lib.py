@@ -22,6 +22,7 @@ FDAS_MAX_N = 1 << 24
 FDAS_RAW_CAP = 16384
 FDAS_MAX_CAND_CAP = 4096
 FDAS_MAX_HARM = 16
+FDAS_NOALLOC_SCRATCH_BYTES = 8 * 8 * (FDAS_RAW_CAP + 4)
 
 
 class fdas_params(C.Structure):
@@ -60,6 +61,7 @@ SIGNATURES = {
     "fdas_harmonic_sum": (C.c_int, [P, VP, SZ, SZ, VP, VP, VP, VP, VP, SZ, VP]),
     "fdas_search": (C.c_int, [P, VP, SZ, VP, VP, SZ, VP, VP, VP, VP, VP, SZ, VP]),
     "fdas_search_host": (C.c_int, [P, VP, SZ, VP, VP, VP, SZ, VP, VP, VP, VP, VP, VP, VP, VP, SZ, VP]),
+    "fdas_harmonic_sum_noalloc": (C.c_int, [P, VP, SZ, SZ, VP, VP, VP, VP, VP]),
 }
 
 _lib = None

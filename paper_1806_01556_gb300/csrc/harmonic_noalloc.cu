@@ -1,0 +1,54 @@
+// fdas_harmonic_sum_noalloc: the harmonic-sum entry point for callers that cannot allocate
+// device memory. Its scratch (crossing counters, per-plane peak keys and raw candidate keys)
+// lives in one file-scope device array instead of a caller-provided workspace. The array is
+// sized for up to 8 harmonic planes (the paper's N_hp) and is held by every GPU that loads
+// the library until the process exits.
+#include <mutex>
+
+#include "fdas_internal.cuh"
+
+namespace {
+
+constexpr size_t kNoallocWords = FDAS_NOALLOC_SCRATCH_BYTES / sizeof(unsigned long long);
+static_assert(FDAS_NOALLOC_SCRATCH_BYTES % sizeof(unsigned long long) == 0, "scratch size in whole words");
+
+// Shared by every call on a device; kernels reach it through the address fetched below.
+static __device__ __align__(256) unsigned long long g_fdas_noalloc_scratch[kNoallocWords];
+
+constexpr int kMaxDevices = 128;
+void *g_scratch_addr[kMaxDevices];  // device address of the array, per device ordinal
+std::mutex g_scratch_mutex;
+
+// In host code g_fdas_noalloc_scratch is only a host-side stand-in for the device array, so its
+// device address is looked up once per device, with that device current.
+cudaError_t scratch_address(void **out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (g_scratch_addr[dev] == nullptr) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_fdas_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" fdas_status fdas_harmonic_sum_noalloc(const fdas_params *p, const float *d_plane, size_t n, size_t ld,
+                                                 const float *d_thresh, fdas_cand *d_cands, uint32_t *d_counts,
+                                                 fdas_cand *d_peaks, fdas_stream_t stream) {
+    fdas_status st = fdas_check_params(p);
+    if (st != FDAS_OK) return st;
+    if (fdas_workspace_bytes(p, n) > FDAS_NOALLOC_SCRATCH_BYTES) return FDAS_ERR_WORKSPACE;
+    void *ws = nullptr;
+    if (scratch_address(&ws) != cudaSuccess) return FDAS_ERR_CUDA;
+    // The harmonic-sum launch sequence zeroes the counters and peak keys before its main kernel,
+    // so whatever an earlier call left in the array does not leak into this one.
+    return fdas_harmonic_sum(p, d_plane, n, ld, d_thresh, d_cands, d_counts, d_peaks, ws,
+                             FDAS_NOALLOC_SCRATCH_BYTES, stream);
+}
