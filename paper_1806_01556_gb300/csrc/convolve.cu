@@ -13,8 +13,11 @@
 // 64-bit accesses. After the forward FFT, thread tid holds frequency m = tid + 128 q in register
 // q. This is exactly the input layout of the inverse FFT's first pass, so the product with the
 // template needs no exchange. The template values are read from global memory (the 1.4 MB bank
-// stays in L2) with coalesced 8-byte loads. After the inverse FFT, thread tid holds time index
+// stays in L2) through a cp.async double buffer in shared memory, so the next template is in flight
+// while the current one is transformed. After the inverse FFT, thread tid holds time index
 // n = tid + 128 q, so the power stores of a warp are 32 consecutive columns.
+#include <utility>
+
 #include "fdas_internal.cuh"
 
 namespace fdas {
@@ -38,6 +41,17 @@ __device__ __forceinline__ float2 twiddle(float2 v, float2 w) {  // w = exp(-2 p
 }
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+
+// Asynchronous 8-byte global -> shared copies (cp.async, completion tracked per thread in groups).
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all_but_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// Global store of one float under a predicate, without a branch.
+__device__ __forceinline__ void st_if(float *p, float v, unsigned pred) {
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q st.global.f32 [%0], %1;\n}\n" ::"l"(p), "f"(v), "r"(pred)
+        : "memory");
+}
 
 // In-place 4-point DFT of (a, b, c, d) with sign exp(-+2 pi i / 4); outputs in natural order.
 template <bool INV>
@@ -144,11 +158,30 @@ __device__ __forceinline__ void fft_pass_3(float2 (&u)[8], const float2 *buf1, c
     dft8<INV>(u);
 }
 
+// Each thread stages exactly the template values it multiplies (frequencies tid + 128 q), so the
+// double-buffered staging needs no barrier: cp.async.wait_group orders a thread's own copies.
+// sdst is the shared-memory address of the thread's first element; both strides are 1 KiB.
+template <int Q>
+__device__ __forceinline__ void cp_async8(unsigned sdst, const float2 *gsrc) {
+    asm volatile("cp.async.ca.shared.global [%0+%2], [%1+%2], 8;\n" ::"r"(sdst), "l"(gsrc), "n"(Q * 1024) : "memory");
+}
+template <int... Q>
+__device__ __forceinline__ void stage_template(unsigned sdst, const float2 *gsrc, std::integer_sequence<int, Q...>) {
+    (cp_async8<Q>(sdst, gsrc), ...);
+}
+__device__ __forceinline__ void stage_template(unsigned sdst, const float2 *gsrc) {
+    stage_template(sdst, gsrc, std::make_integer_sequence<int, 16>{});
+}
+
+constexpr size_t kSmemBytes = (2 * kPadded + 2 * kF) * sizeof(float2);  // two exchange + two template buffers
+
 __global__ void __launch_bounds__(kThreads, 3)
     fdas_ols_fp32(const float2 *__restrict__ spec, int n, const float2 *__restrict__ tmpl, int n_temp, int h, int keep,
                   float *__restrict__ plane, size_t ld, int n_seg, int t_chunk, int n_tchunk) {
-    __shared__ float2 buf0[kPadded];
-    __shared__ float2 buf1[kPadded];
+    extern __shared__ float2 smem[];
+    float2 *buf0 = smem;
+    float2 *buf1 = smem + kPadded;
+    float2 *tbuf = smem + 2 * kPadded;  // [2][kF], template values of the current and next template
     const int tid = threadIdx.x;
     const float2 *wtab = tmpl + (size_t)n_temp * kF;  // exp(-2 pi i k / F)
 
@@ -164,6 +197,16 @@ __global__ void __launch_bounds__(kThreads, 3)
             tw3b[r] = __ldg(&wtab[(tid + 128) * r]);
         }
     }
+    // Output register (hh, r) holds segment time index m = tid + 128 hh + 256 r; it is a valid
+    // (non-wrapped) overlap-save output iff h <= m < h + keep. Bit 8 hh + r of keep_mask.
+    unsigned keep_mask = 0u;
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh)
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int m = tid + 128 * hh + 256 * r;
+            if (m >= h && m < h + keep) keep_mask |= 1u << (8 * hh + r);
+        }
     const float scale = 1.0f / kF;
     const int n_items = n_seg * n_tchunk;
 
@@ -171,7 +214,21 @@ __global__ void __launch_bounds__(kThreads, 3)
         const int s = item / n_tchunk;
         const int t0 = (item - s * n_tchunk) * t_chunk;
         const int t1 = min(t0 + t_chunk, n_temp);
-        const int origin = s * keep - h;  // input index of segment point 0
+        const int origin = s * keep - h;               // input index of segment point 0
+        const int col0 = s * keep - h;                 // column of segment time index 0
+        // Outputs this thread stores for this segment: valid (keep_mask) and inside the spectrum.
+        unsigned smask = keep_mask;
+        if ((s + 1) * keep > n) {
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh)
+#pragma unroll
+                for (int r = 0; r < 8; ++r)
+                    if (col0 + tid + 128 * hh + 256 * r >= n) smask &= ~(1u << (8 * hh + r));
+        }
+        const unsigned tb0 = (unsigned)__cvta_generic_to_shared(tbuf + tid);
+        const unsigned tb1 = tb0 + kF * (unsigned)sizeof(float2);
+        stage_template(tb0, tmpl + (size_t)t0 * kF + tid);  // lands while the forward FFT runs
+        cp_async_commit();
 
         // Forward FFT of the segment: W[q] = DFT(w_s)[tid + 128 q] / F.
         float2 v[16];
@@ -193,9 +250,14 @@ __global__ void __launch_bounds__(kThreads, 3)
         }
 
         for (int t = t0; t < t1; ++t) {
-            const float2 *T = tmpl + (size_t)t * kF + tid;
+            const int slot = (t - t0) & 1;
+            // Stage the next template (the last one again on the final iteration: no branch).
+            stage_template(slot ? tb0 : tb1, tmpl + (size_t)min(t + 1, t1 - 1) * kF + tid);
+            cp_async_commit();
+            cp_async_wait_all_but_one();  // this thread's copies of template t have landed
+            const float2 *T = tbuf + slot * kF + tid;
 #pragma unroll
-            for (int q = 0; q < 16; ++q) v[q] = cmul(W[q], __ldg(&T[128 * q]));
+            for (int q = 0; q < 16; ++q) v[q] = cmul(W[q], T[128 * q]);
             fft_passes_12<true>(v, buf0, buf1, tw2, tid);
             float *row = plane + (size_t)t * ld;
 #pragma unroll
@@ -204,11 +266,8 @@ __global__ void __launch_bounds__(kThreads, 3)
                 const int b = tid + 128 * hh;
                 fft_pass_3<true>(u, buf1, hh ? tw3b : tw3a, b);
 #pragma unroll
-                for (int r = 0; r < 8; ++r) {
-                    const int m = b + 256 * r;  // time index within the segment
-                    const int col = s * keep + m - h;
-                    if (m >= h && m < h + keep && col < n) row[col] = fmaf(u[r].x, u[r].x, u[r].y * u[r].y);
-                }
+                for (int r = 0; r < 8; ++r)
+                    st_if(row + col0 + b + 256 * r, fmaf(u[r].x, u[r].x, u[r].y * u[r].y), (smask >> (8 * hh + r)) & 1u);
             }
         }
     }
@@ -222,8 +281,10 @@ cudaError_t launch_convolve_fp32(const Geometry &g, const float2 *spec, size_t n
     const int t_chunk = g.n_temp;  // one work item per segment: forward FFT once, all templates
     const int n_tchunk = (g.n_temp + t_chunk - 1) / t_chunk;
     const int n_items = n_seg * n_tchunk;
-    fdas_ols_fp32<<<n_items, kThreads, 0, s>>>(spec, (int)n, tmpl, g.n_temp, g.h, g.keep, plane, ld, n_seg, t_chunk,
-                                                n_tchunk);
+    cudaError_t e = cudaFuncSetAttribute(fdas_ols_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    if (e != cudaSuccess) return e;
+    fdas_ols_fp32<<<n_items, kThreads, kSmemBytes, s>>>(spec, (int)n, tmpl, g.n_temp, g.h, g.keep, plane, ld, n_seg,
+                                                         t_chunk, n_tchunk);
     return cudaGetLastError();
 }
 

@@ -7,15 +7,17 @@
 //
 // GB300 mapping:
 //   fdas_hs_reset    zeroes the per-plane crossing counters and peak keys in the workspace.
-//   fdas_hs          grid (column blocks, plane rows). Each thread handles 4 fundamentals of one
-//                    row (2 when more than 8 planes are summed), j = j0 + tid + 256 u. It issues
-//                    every strided gather P[c + l i][l j] before summing, so many loads are in
-//                    flight, and reads through the read-only path. Crossings are compacted warp by warp: a ballot, one atomicAdd per warp,
-//                    and a prefix popcount for each lane's slot. Each candidate is stored as one
-//                    64-bit key whose ascending order is the canonical order
-//                    (power desc, i asc, j asc). The loudest point of every plane is kept per
-//                    thread, reduced across the warp with shuffles, and merged with one 64-bit
-//                    atomicMax per warp.
+//   fdas_hs_k1/kl<K> one launch per group of rows that take part in the same number K of planes
+//                    (K = min(n_harm, floor(c/|i|))), each compiled for exactly K terms; grid
+//                    (column blocks of 1024 fundamentals, rows of the group). Rows with one plane
+//                    stream 16-byte loads, 4096 columns per CTA. The others issue every strided
+//                    gather P[c + l i][l j] of a thread's 4 fundamentals before summing, through
+//                    the read-only path. Crossings are rare and take a separate path: a ballot, one
+//                    atomicAdd per warp, and a prefix popcount for each lane's slot. Each candidate
+//                    is one 64-bit key whose ascending order is the canonical order (power desc,
+//                    i asc, j asc). The loudest point of every plane comes from warp reductions
+//                    (redux max of the power bits, then redux min of the column), a block merge in
+//                    shared memory, and at most one 64-bit atomicMax per block and plane.
 //   fdas_hs_finalize one CTA per plane. It bitonic-sorts the raw keys in shared memory, then decodes
 //                    the top cand_cap keys into fdas_cand records and writes the counts and peaks.
 #include "fdas_internal.cuh"
@@ -45,89 +47,244 @@ __global__ void fdas_hs_reset(unsigned long long *counters, unsigned long long *
     }
 }
 
-// Fundamentals per thread: fewer when more planes are summed, to keep the gathers in registers.
-template <int KMAX>
-__host__ __device__ constexpr int hs_jpt() { return KMAX <= 8 ? 4 : 2; }
+constexpr int kHsWarps = kHsThreads / 32;
+constexpr int kJpt = 4;                          // fundamentals per thread
+constexpr int kColsPerBlock = kHsThreads * kJpt;  // 1024 fundamental columns per CTA
 
-template <int KMAX>
-__global__ void __launch_bounds__(kHsThreads)
-    fdas_hs(const float *__restrict__ plane, int n, size_t ld, const float *__restrict__ thresh, int n_temp,
-            int n_harm, unsigned mask, unsigned long long *__restrict__ raw, unsigned long long *counters,
-            unsigned long long *peaks) {
-    const int c = (n_temp - 1) / 2;
-    const int row = blockIdx.y;  // c + i
-    const int i = row - c;
-    const int ai = i < 0 ? -i : i;
-    // Planes k with |k i| <= c exist in this row. All of them are summed (the peak of every plane
-    // is reported), and candidates are emitted for the planes selected by mask.
-    const int klast = (ai == 0) ? n_harm : min(n_harm, c / ai);
-    const int jend = n;
-    constexpr int kJpt = hs_jpt<KMAX>();
-    const int j0 = blockIdx.x * (kHsThreads * kJpt);
-
-    const int lane = threadIdx.x & 31;
-    float best[KMAX];
-    unsigned bestj[KMAX];
-#pragma unroll
-    for (int k = 0; k < KMAX; ++k) {
-        best[k] = -1.0f;
-        bestj[k] = 0u;
+// Warp-wide candidate compaction: one ballot, one atomicAdd per warp, a prefix popcount per lane.
+__device__ __forceinline__ void emit(bool hit, float hp, int row, unsigned j, int plane_k, int lane,
+                                     unsigned long long *counters, unsigned long long *raw) {
+    const unsigned ballot = __ballot_sync(0xFFFFFFFFu, hit);
+    if (!ballot) return;
+    const int leader = __ffs(ballot) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(&counters[plane_k - 1], (unsigned long long)__popc(ballot));
+    base = __shfl_sync(0xFFFFFFFFu, base, leader);
+    if (hit) {
+        const unsigned long long slot = base + __popc(ballot & ((1u << lane) - 1u));
+        if (slot < FDAS_RAW_CAP) raw[(size_t)(plane_k - 1) * FDAS_RAW_CAP + slot] = cand_key(hp, row, j);
     }
+}
 
-    // Gather every term of every fundamental of this thread first.
-    float v[kJpt][KMAX];
-    int km[kJpt];
+// The loudest point of plane k over a warp: redux max of the power bits (non-negative floats order
+// like their bits), then redux min of the column among the lanes that hold that power.
+__device__ __forceinline__ unsigned long long warp_peak_key(float best, int bestj, int row) {
+    const unsigned pb = best >= 0.0f ? __float_as_uint(best) : 0u;
+    const unsigned mx = __reduce_max_sync(0xFFFFFFFFu, pb);
+    const unsigned jmin = __reduce_min_sync(0xFFFFFFFFu, (best >= 0.0f && pb == mx) ? (unsigned)bestj : 0xFFFFFFFFu);
+    if (jmin == 0xFFFFFFFFu) return 0ull;
+    return peak_key(__uint_as_float(mx), row, jmin);
+}
+
+// Block-level merge of the warps' peak keys and one atomicMax per block and plane, skipped when the
+// block's key cannot win (peak keys only grow).
+template <int KL>
+__device__ __forceinline__ void block_peaks(const unsigned long long (&key)[KL], unsigned long long *peaks) {
+    __shared__ unsigned long long warp_key[kHsWarps][KL];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
 #pragma unroll
-    for (int u = 0; u < kJpt; ++u) {
-        const int j = j0 + threadIdx.x + kHsThreads * u;
-        int terms = 0;
-        if (j < jend) terms = (j == 0) ? klast : min(klast, (n - 1) / j);
-        km[u] = terms;
+        for (int k = 0; k < KL; ++k) warp_key[warp][k] = key[k];
+    }
+    __syncthreads();
+    if (threadIdx.x < KL) {
+        unsigned long long m = 0ull;
 #pragma unroll
-        for (int l = 1; l <= KMAX; ++l) {
-            if (l <= terms) v[u][l - 1] = __ldg(plane + (size_t)(c + l * i) * ld + (size_t)l * j);
+        for (int w = 0; w < kHsWarps; ++w) m = warp_key[w][threadIdx.x] > m ? warp_key[w][threadIdx.x] : m;
+        if (m > *(volatile unsigned long long *)&peaks[threadIdx.x]) atomicMax(&peaks[threadIdx.x], m);
+    }
+}
+
+// Rows with a single plane (|2 i| > c): HP_1 = P. Each thread streams kK1Vec groups of 4
+// consecutive columns, one 16-byte load each when the row stride allows it.
+constexpr int kK1Vec = 4;
+constexpr int kK1Cols = kHsThreads * 4 * kK1Vec;  // 4096 columns per CTA
+
+__device__ __forceinline__ void hs_row_k1(const float *__restrict__ prow, int n, float ta, int row, int j0,
+                                          unsigned long long *raw, unsigned long long *counters,
+                                          unsigned long long *peaks, bool vec) {
+    const int lane = threadIdx.x & 31;
+    float v[kK1Vec][4];
+#pragma unroll
+    for (int g = 0; g < kK1Vec; ++g) {
+        const int jt = j0 + 4 * (threadIdx.x + kHsThreads * g);
+        if (vec && jt + 3 < n) {
+            const float4 q = __ldg(reinterpret_cast<const float4 *>(prow + jt));
+            v[g][0] = q.x, v[g][1] = q.y, v[g][2] = q.z, v[g][3] = q.w;
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[g][u] = (jt + u < n) ? __ldg(prow + jt + u) : -1.0f;
         }
     }
+    float best = -1.0f;
+    int bestj = 0;
+    bool any_hit = false;
+#pragma unroll
+    for (int g = 0; g < kK1Vec; ++g)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const bool gt = v[g][u] > best;  // invalid columns hold -1 and never win
+            best = gt ? v[g][u] : best;
+            bestj = gt ? j0 + 4 * (threadIdx.x + kHsThreads * g) + u : bestj;
+            any_hit |= v[g][u] > ta;
+        }
+    if (__any_sync(0xFFFFFFFFu, any_hit)) {
+#pragma unroll
+        for (int g = 0; g < kK1Vec; ++g)
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                emit(v[g][u] > ta, v[g][u], row, (unsigned)(j0 + 4 * (threadIdx.x + kHsThreads * g) + u), 1, lane,
+                     counters, raw);
+    }
+    unsigned long long key[1] = {warp_peak_key(best, bestj, row)};
+    block_peaks<1>(key, peaks);
+}
 
+// Rows with KL >= 2 planes: lane L of warp w handles j = j0 + 32 kJpt w + L + 32 u. Every gather of a
+// warp is one coalesced stride-l access along a plane row. FULL: every fundamental of the warp has
+// all KL terms (l j <= n-1 for l <= KL), which holds everywhere except near the domain edges.
+template <int KL, bool FULL>
+__device__ __forceinline__ void hs_row_body(const float *const (&rp)[KL], const float (&ta)[KL], int n, int row,
+                                            int jbase, int lane, unsigned long long *raw,
+                                            unsigned long long *counters, unsigned long long (&key)[KL]) {
+    float v[kJpt][KL];
+    int terms[kJpt];
 #pragma unroll
     for (int u = 0; u < kJpt; ++u) {
-        const unsigned j = (unsigned)(j0 + threadIdx.x + kHsThreads * u);
+        const int j = jbase + 32 * u;
+        int t = KL;
+        if (!FULL) {
+            t = 0;
+            if (j < n) {
+#pragma unroll
+                for (int l = 1; l <= KL; ++l)
+                    if ((long long)l * j <= (long long)(n - 1)) t = l;
+            }
+        }
+        terms[u] = t;
+    }
+#pragma unroll
+    for (int u = 0; u < kJpt; ++u)
+#pragma unroll
+        for (int l = 1; l <= KL; ++l)
+            v[u][l - 1] = (FULL || l <= terms[u]) ? __ldg(rp[l - 1] + (size_t)l * (jbase + 32 * u)) : 0.0f;
+    // HP_k = HP_{k-1} + P[c + k i][k j] in float32, k = 1, 2, ..., with each thread's best point per plane.
+    float best[KL];
+    int bestj[KL];
+#pragma unroll
+    for (int l = 0; l < KL; ++l) {
+        best[l] = -1.0f;
+        bestj[l] = 0;
+    }
+    bool any_hit = false;
+#pragma unroll
+    for (int u = 0; u < kJpt; ++u) {
+        const int j = jbase + 32 * u;
         float hp = 0.0f;
 #pragma unroll
-        for (int k = 1; k <= KMAX; ++k) {
-            if (k > klast) break;  // block-uniform
-            const bool valid = k <= km[u];
-            if (valid) hp = (k == 1) ? v[u][0] : __fadd_rn(hp, v[u][k - 1]);
-            if (valid && hp > best[k - 1]) {
-                best[k - 1] = hp;
-                bestj[k - 1] = j;
-            }
-            const bool hit = valid && ((mask >> (k - 1)) & 1u) && hp > __ldg(&thresh[(k - 1) * n_temp + row]);
-            const unsigned ballot = __ballot_sync(0xFFFFFFFFu, hit);
-            if (ballot) {
-                const int leader = __ffs(ballot) - 1;
-                unsigned long long base = 0;
-                if (lane == leader) base = atomicAdd(&counters[k - 1], (unsigned long long)__popc(ballot));
-                base = __shfl_sync(0xFFFFFFFFu, base, leader);
-                if (hit) {
-                    const unsigned long long slot = base + __popc(ballot & ((1u << lane) - 1u));
-                    if (slot < FDAS_RAW_CAP) raw[(size_t)(k - 1) * FDAS_RAW_CAP + slot] = cand_key(hp, row, j);
-                }
+        for (int l = 1; l <= KL; ++l) {
+            hp = (l == 1) ? v[u][0] : __fadd_rn(hp, v[u][l - 1]);
+            const bool ok = FULL || l <= terms[u];
+            const bool gt = ok && hp > best[l - 1];
+            best[l - 1] = gt ? hp : best[l - 1];
+            bestj[l - 1] = gt ? j : bestj[l - 1];
+            any_hit |= ok && hp > ta[l - 1];
+        }
+    }
+    // Rare path: recompute the same sums and compact the crossings.
+    if (__any_sync(0xFFFFFFFFu, any_hit)) {
+#pragma unroll
+        for (int u = 0; u < kJpt; ++u) {
+            const unsigned j = (unsigned)(jbase + 32 * u);
+            float hp = 0.0f;
+#pragma unroll
+            for (int l = 1; l <= KL; ++l) {
+                hp = (l == 1) ? v[u][0] : __fadd_rn(hp, v[u][l - 1]);
+                emit((FULL || l <= terms[u]) && hp > ta[l - 1], hp, row, j, l, lane, counters, raw);
             }
         }
     }
+#pragma unroll
+    for (int l = 0; l < KL; ++l) key[l] = warp_peak_key(best[l], bestj[l], row);
+}
 
-    // Loudest point per plane: warp-shuffle max of the 64-bit peak key, one atomicMax per warp.
+template <int KL>
+__device__ __forceinline__ void hs_row(const float *__restrict__ plane, int n, size_t ld, const float *__restrict__ thresh,
+                                       int n_temp, unsigned mask, int c, int i, int j0, unsigned long long *raw,
+                                       unsigned long long *counters, unsigned long long *peaks) {
+    const int row = c + i;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int jw = j0 + warp * (32 * kJpt);
+    const float *rp[KL];
+    float ta[KL];
 #pragma unroll
-    for (int k = 1; k <= KMAX; ++k) {
-        if (k > klast) break;
-        unsigned long long key = best[k - 1] >= 0.0f ? peak_key(best[k - 1], row, bestj[k - 1]) : 0ull;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            const unsigned long long o = __shfl_xor_sync(0xFFFFFFFFu, key, off);
-            key = o > key ? o : key;
-        }
-        if (lane == 0 && key) atomicMax(&peaks[k - 1], key);
+    for (int l = 1; l <= KL; ++l) {
+        rp[l - 1] = plane + (size_t)(c + l * i) * ld;
+        ta[l - 1] = ((mask >> (l - 1)) & 1u) ? __ldg(&thresh[(l - 1) * n_temp + row]) : __int_as_float(0x7f800000);
+    }
+    unsigned long long key[KL];
+    if ((long long)(jw + 32 * kJpt - 1) * KL <= (long long)(n - 1))  // warp-uniform
+        hs_row_body<KL, true>(rp, ta, n, row, jw + lane, lane, raw, counters, key);
+    else
+        hs_row_body<KL, false>(rp, ta, n, row, jw + lane, lane, raw, counters, key);
+    block_peaks<KL>(key, peaks);
+}
+
+// Row i of a group with klast planes: |i| runs over [lo, hi], both signs, and i = 0 when lo == 0.
+__device__ __forceinline__ int group_row_offset(int y, int lo) {
+    if (lo == 0) {
+        if (y == 0) return 0;
+        const int a = (y + 1) >> 1;  // 1, 1, 2, 2, ...
+        return (y & 1) ? -a : a;
+    }
+    const int a = lo + (y >> 1);
+    return (y & 1) ? a : -a;
+}
+
+// One launch per group of rows sharing klast = min(n_harm, floor(c/|i|)) planes, so each kernel is
+// compiled for exactly its number of terms. Grid: (column blocks of 1024 fundamentals, rows of the group).
+__global__ void __launch_bounds__(kHsThreads, 4)
+    fdas_hs_k1(const float *__restrict__ plane, int n, size_t ld, const float *__restrict__ thresh, int n_temp,
+               unsigned mask, int lo, unsigned long long *__restrict__ raw, unsigned long long *counters,
+               unsigned long long *peaks) {
+    const int c = (n_temp - 1) / 2;
+    const int row = c + group_row_offset(blockIdx.y, lo);
+    const float ta = (mask & 1u) ? __ldg(&thresh[row]) : __int_as_float(0x7f800000);
+    const bool vec = (ld & 3) == 0 && (reinterpret_cast<uintptr_t>(plane) & 15) == 0;
+    hs_row_k1(plane + (size_t)row * ld, n, ta, row, blockIdx.x * kK1Cols, raw, counters, peaks, vec);
+}
+
+template <int KL>
+__global__ void __launch_bounds__(kHsThreads, KL <= 3 ? 4 : 2)
+    fdas_hs_kl(const float *__restrict__ plane, int n, size_t ld, const float *__restrict__ thresh, int n_temp,
+               unsigned mask, int lo, unsigned long long *__restrict__ raw, unsigned long long *counters,
+               unsigned long long *peaks) {
+    const int c = (n_temp - 1) / 2;
+    hs_row<KL>(plane, n, ld, thresh, n_temp, mask, c, group_row_offset(blockIdx.y, lo), blockIdx.x * kColsPerBlock,
+               raw, counters, peaks);
+}
+
+using HsKernel = void (*)(const float *, int, size_t, const float *, int, unsigned, int, unsigned long long *,
+                          unsigned long long *, unsigned long long *);
+
+HsKernel hs_kernel(int klast) {
+    switch (klast) {
+        case 1: return fdas_hs_k1;
+        case 2: return fdas_hs_kl<2>;
+        case 3: return fdas_hs_kl<3>;
+        case 4: return fdas_hs_kl<4>;
+        case 5: return fdas_hs_kl<5>;
+        case 6: return fdas_hs_kl<6>;
+        case 7: return fdas_hs_kl<7>;
+        case 8: return fdas_hs_kl<8>;
+        case 9: return fdas_hs_kl<9>;
+        case 10: return fdas_hs_kl<10>;
+        case 11: return fdas_hs_kl<11>;
+        case 12: return fdas_hs_kl<12>;
+        case 13: return fdas_hs_kl<13>;
+        case 14: return fdas_hs_kl<14>;
+        case 15: return fdas_hs_kl<15>;
+        default: return fdas_hs_kl<16>;
     }
 }
 
@@ -197,19 +354,21 @@ cudaError_t launch_harmonic(const fdas_params &p, const float *plane, size_t n, 
     fdas_hs_reset<<<1, 32, 0, s>>>(ws.counters, ws.peaks, p.n_harm);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if (p.n_harm <= 8) {
-        constexpr int per = kHsThreads * hs_jpt<8>();
-        dim3 grid((unsigned)((n + per - 1) / per), (unsigned)p.n_temp);
-        fdas_hs<8><<<grid, kHsThreads, 0, s>>>(plane, (int)n, ld, thresh, p.n_temp, p.n_harm, p.harm_mask, ws.raw,
-                                               ws.counters, ws.peaks);
-    } else {
-        constexpr int per = kHsThreads * hs_jpt<FDAS_MAX_HARM>();
-        dim3 grid((unsigned)((n + per - 1) / per), (unsigned)p.n_temp);
-        fdas_hs<FDAS_MAX_HARM><<<grid, kHsThreads, 0, s>>>(plane, (int)n, ld, thresh, p.n_temp, p.n_harm, p.harm_mask,
-                                                           ws.raw, ws.counters, ws.peaks);
+    // Rows grouped by their number of planes klast: klast = n_harm for |i| <= c / n_harm, and
+    // klast = K < n_harm for c/(K+1) < |i| <= c/K.
+    const int c = (p.n_temp - 1) / 2;
+    const unsigned gx = (unsigned)((n + kColsPerBlock - 1) / kColsPerBlock);
+    for (int K = p.n_harm; K >= 1; --K) {
+        const int lo = (K == p.n_harm) ? 0 : c / (K + 1) + 1;
+        const int hi = c / K;
+        if (hi < lo) continue;
+        const int rows = (lo == 0) ? 2 * hi + 1 : 2 * (hi - lo + 1);
+        const unsigned gxk = (K == 1) ? (unsigned)((n + kK1Cols - 1) / kK1Cols) : gx;
+        hs_kernel(K)<<<dim3(gxk, (unsigned)rows), kHsThreads, 0, s>>>(plane, (int)n, ld, thresh, p.n_temp, p.harm_mask,
+                                                                    lo, ws.raw, ws.counters, ws.peaks);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
     }
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
     const int smem = FDAS_RAW_CAP * (int)sizeof(unsigned long long);
     e = cudaFuncSetAttribute(fdas_hs_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
