@@ -44,6 +44,8 @@ extern "C" fdas_status fdas_harmonic_sum_noalloc(const fdas_params *p, const flo
                                                  fdas_cand *d_peaks, fdas_stream_t stream) {
     fdas_status st = fdas_check_params(p);
     if (st != FDAS_OK) return st;
+    // Same argument checks as fdas_harmonic_sum, before the device address is looked up.
+    if (n < 1 || n > FDAS_MAX_N || ld < n || !d_plane || !d_thresh || !d_cands || !d_counts) return FDAS_ERR_INVALID_ARG;
     if (fdas_workspace_bytes(p, n) > FDAS_NOALLOC_SCRATCH_BYTES) return FDAS_ERR_WORKSPACE;
     void *ws = nullptr;
     if (scratch_address(&ws) != cudaSuccess) return FDAS_ERR_CUDA;

@@ -122,3 +122,31 @@ def test_bad_pointers_are_rejected_before_any_launch(fd):
                                 null, fake, ws, null) == -1
     assert lib.fdas_default_thresholds(C.byref(p), 6.0, 2, fake) == -1
     assert lib.fdas_status_string(-3) == b"workspace too small"
+
+
+class _NullStream:
+    cuda_stream = 0
+
+
+def test_python_wrappers_marshal_and_raise_on_rejected_arguments(fd):
+    """Every binding wrapper reaches its C entry point; n = 0 is rejected before any CUDA call."""
+    import numpy as np
+
+    p = fd.Params()
+    buf = np.zeros(64, dtype=np.float32)
+    st = _NullStream()
+    calls = [
+        lambda: fd.fdas_convolve(p, buf, 0, buf, buf, 0, st),
+        lambda: fd.fdas_convolve_cfg(p, buf, 0, buf, buf, 0, 2, 17, st),
+        lambda: fd.fdas_harmonic_sum(p, buf, 0, 0, buf, buf, buf, None, buf, 1 << 30, st),
+        lambda: fd.fdas_search(p, buf, 0, buf, buf, 0, buf, buf, buf, None, buf, 1 << 30, st),
+        lambda: fd.fdas_search_host(p, buf, 0, buf, buf, buf, 0, buf, buf, buf, None, buf, buf, None, buf, 1 << 30, st),
+        lambda: fd.fdas_harmonic_sum_noalloc(p, buf, 0, 0, buf, buf, buf, None, st),
+        lambda: fd.fdas_make_templates(fd.Params(n_temp=4), buf, st),
+    ]
+    for call in calls:
+        with pytest.raises(fd.FdasError) as err:
+            call()
+        assert err.value.status == -1
+    bad = fd.Params(n_temp=84)
+    assert fd.fdas_templates_bytes(bad) == 0 and fd.fdas_workspace_bytes(bad, 10) == 0
