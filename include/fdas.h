@@ -182,6 +182,27 @@ fdas_status fdas_harmonic_sum(const fdas_params *p, const float *d_plane, size_t
                               const float *d_thresh, fdas_cand *d_cands, uint32_t *d_counts,
                               fdas_cand *d_peaks, void *d_ws, size_t ws_bytes, fdas_stream_t stream);
 
+/*
+ * Launch shape of the convolution kernel (not part of the method; the paper's counterpart is the
+ * compile-time parallelisation factor of its OpenCL kernels, Sec. 3.3 "Parallelisation Factor").
+ *   ctas_per_sm           0: one CTA per work item, as many resident as fit (3 per SM). k > 0: a
+ *                         persistent grid of k CTAs per SM that loop over the work items, which leaves
+ *                         room on every SM for kernels of other streams (e.g. the harmonic sum of the
+ *                         previous spectrum).
+ *   templates_per_item    0: a work item is one segment with all n_temp templates (the segment is
+ *                         transformed once). k > 0: items of k templates; each item transforms its
+ *                         segment again, which gives more, smaller items.
+ * Results do not depend on the launch shape.
+ */
+typedef struct {
+    int32_t ctas_per_sm;
+    int32_t templates_per_item;
+} fdas_launch_config;
+
+/* fdas_convolve with an explicit launch shape (NULL = the defaults, as fdas_convolve). */
+fdas_status fdas_convolve_cfg(const fdas_params *p, const void *d_spec, size_t n, const void *d_tmpl, float *d_plane,
+                              size_t ld, const fdas_launch_config *cfg, fdas_stream_t stream);
+
 /* fdas_convolve followed by fdas_harmonic_sum on the same stream: the whole FDAS path for one
  * spectrum (Sec. 3.1, Eq. t_FDAS, with no separate FOP preparation). */
 fdas_status fdas_search(const fdas_params *p, const void *d_spec, size_t n, const void *d_tmpl,

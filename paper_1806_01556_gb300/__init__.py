@@ -30,6 +30,7 @@ __all__ = [
     "fdas_default_thresholds",
     "fdas_make_templates",
     "fdas_convolve",
+    "fdas_convolve_cfg",
     "fdas_harmonic_sum",
     "fdas_search",
     "fdas_search_host",
@@ -124,6 +125,16 @@ def fdas_convolve(p: Params, d_spec, n: int, d_tmpl, d_plane, ld: int, stream=No
     _check(
         lib().fdas_convolve(C.byref(p.c()), _ptr(d_spec), n, _ptr(d_tmpl), _ptr(d_plane), ld, _stream(stream)),
         "fdas_convolve",
+    )
+
+
+def fdas_convolve_cfg(p: Params, d_spec, n: int, d_tmpl, d_plane, ld: int, ctas_per_sm: int = 0,
+                      templates_per_item: int = 0, stream=None) -> None:
+    cfg = _lib.fdas_launch_config(ctas_per_sm, templates_per_item)
+    _check(
+        lib().fdas_convolve_cfg(C.byref(p.c()), _ptr(d_spec), n, _ptr(d_tmpl), _ptr(d_plane), ld, C.byref(cfg),
+                                _stream(stream)),
+        "fdas_convolve_cfg",
     )
 
 

@@ -39,6 +39,10 @@ class fdas_params(C.Structure):
     ]
 
 
+class fdas_launch_config(C.Structure):
+    _fields_ = [("ctas_per_sm", C.c_int32), ("templates_per_item", C.c_int32)]
+
+
 class fdas_cand(C.Structure):
     _fields_ = [("power", C.c_float), ("j", C.c_uint32), ("i", C.c_int16), ("k", C.c_uint8), ("pad", C.c_uint8)]
 
@@ -58,6 +62,7 @@ SIGNATURES = {
     "fdas_default_thresholds": (C.c_int, [P, C.c_double, C.c_int, VP]),
     "fdas_make_templates": (C.c_int, [P, VP, VP]),
     "fdas_convolve": (C.c_int, [P, VP, SZ, VP, VP, SZ, VP]),
+    "fdas_convolve_cfg": (C.c_int, [P, VP, SZ, VP, VP, SZ, VP, VP]),
     "fdas_harmonic_sum": (C.c_int, [P, VP, SZ, SZ, VP, VP, VP, VP, VP, SZ, VP]),
     "fdas_search": (C.c_int, [P, VP, SZ, VP, VP, SZ, VP, VP, VP, VP, VP, SZ, VP]),
     "fdas_search_host": (C.c_int, [P, VP, SZ, VP, VP, VP, SZ, VP, VP, VP, VP, VP, VP, VP, VP, SZ, VP]),

@@ -122,16 +122,24 @@ fdas_status fdas_make_templates(const fdas_params *p, void *d_tmpl, fdas_stream_
     return cuda_status(fdas::launch_templates(*p, d_tmpl, stream));
 }
 
-fdas_status fdas_convolve(const fdas_params *p, const void *d_spec, size_t n, const void *d_tmpl, float *d_plane,
-                          size_t ld, fdas_stream_t stream) {
+fdas_status fdas_convolve_cfg(const fdas_params *p, const void *d_spec, size_t n, const void *d_tmpl, float *d_plane,
+                              size_t ld, const fdas_launch_config *cfg, fdas_stream_t stream) {
     fdas_status st = fdas_check_params(p);
     if (st != FDAS_OK) return st;
     if ((st = check_shape(p, n, ld)) != FDAS_OK) return st;
     if (!d_spec || !d_tmpl || !d_plane) return FDAS_ERR_INVALID_ARG;
     if (!aligned16(d_spec) || !aligned16(d_tmpl) || !aligned16(d_plane)) return FDAS_ERR_INVALID_ARG;
+    const int ctas = cfg ? cfg->ctas_per_sm : 0;
+    const int tpi = cfg ? cfg->templates_per_item : 0;
+    if (ctas < 0 || ctas > 64 || tpi < 0) return FDAS_ERR_INVALID_ARG;
     const Geometry g = fdas::geometry(*p);
     return cuda_status(fdas::launch_convolve_fp32(g, static_cast<const float2 *>(d_spec), n,
-                                                  static_cast<const float2 *>(d_tmpl), d_plane, ld, stream));
+                                                  static_cast<const float2 *>(d_tmpl), d_plane, ld, ctas, tpi, stream));
+}
+
+fdas_status fdas_convolve(const fdas_params *p, const void *d_spec, size_t n, const void *d_tmpl, float *d_plane,
+                          size_t ld, fdas_stream_t stream) {
+    return fdas_convolve_cfg(p, d_spec, n, d_tmpl, d_plane, ld, nullptr, stream);
 }
 
 fdas_status fdas_harmonic_sum(const fdas_params *p, const float *d_plane, size_t n, size_t ld, const float *d_thresh,

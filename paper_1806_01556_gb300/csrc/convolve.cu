@@ -276,15 +276,24 @@ __global__ void __launch_bounds__(kThreads, 3)
 }  // namespace
 
 cudaError_t launch_convolve_fp32(const Geometry &g, const float2 *spec, size_t n, const float2 *tmpl, float *plane,
-                                 size_t ld, cudaStream_t s) {
+                                 size_t ld, int ctas_per_sm, int templates_per_item, cudaStream_t s) {
     const int n_seg = (int)((n + g.keep - 1) / g.keep);
-    const int t_chunk = g.n_temp;  // one work item per segment: forward FFT once, all templates
+    // A work item is one segment with t_chunk templates; the segment's forward FFT is done once per item.
+    const int t_chunk = (templates_per_item > 0 && templates_per_item < g.n_temp) ? templates_per_item : g.n_temp;
     const int n_tchunk = (g.n_temp + t_chunk - 1) / t_chunk;
     const int n_items = n_seg * n_tchunk;
+    int grid = n_items;
+    if (ctas_per_sm > 0) {
+        int dev = 0, sms = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        grid = n_items < ctas_per_sm * sms ? n_items : ctas_per_sm * sms;
+    }
     cudaError_t e = cudaFuncSetAttribute(fdas_ols_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
     if (e != cudaSuccess) return e;
-    fdas_ols_fp32<<<n_items, kThreads, kSmemBytes, s>>>(spec, (int)n, tmpl, g.n_temp, g.h, g.keep, plane, ld, n_seg,
-                                                         t_chunk, n_tchunk);
+    fdas_ols_fp32<<<grid, kThreads, kSmemBytes, s>>>(spec, (int)n, tmpl, g.n_temp, g.h, g.keep, plane, ld, n_seg,
+                                                      t_chunk, n_tchunk);
     return cudaGetLastError();
 }
 

@@ -50,7 +50,7 @@ inline size_t hs_workspace_words(int n_harm) { return (size_t)n_harm * (FDAS_RAW
 // Kernel launchers (each returns cudaGetLastError() of its launch).
 cudaError_t launch_templates(const fdas_params &p, void *d_tmpl, cudaStream_t s);
 cudaError_t launch_convolve_fp32(const Geometry &g, const float2 *spec, size_t n, const float2 *tmpl,
-                                 float *plane, size_t ld, cudaStream_t s);
+                                 float *plane, size_t ld, int ctas_per_sm, int templates_per_item, cudaStream_t s);
 cudaError_t launch_harmonic(const fdas_params &p, const float *plane, size_t n, size_t ld,
                             const float *thresh, fdas_cand *cands, uint32_t *counts, fdas_cand *peaks,
                             const HsWorkspace &ws, cudaStream_t s);

@@ -118,7 +118,6 @@ __device__ __forceinline__ void hs_row_k1(const float *__restrict__ prow, int n,
     }
     float best = -1.0f;
     int bestj = 0;
-    bool any_hit = false;
 #pragma unroll
     for (int g = 0; g < kK1Vec; ++g)
 #pragma unroll
@@ -126,9 +125,8 @@ __device__ __forceinline__ void hs_row_k1(const float *__restrict__ prow, int n,
             const bool gt = v[g][u] > best;  // invalid columns hold -1 and never win
             best = gt ? v[g][u] : best;
             bestj = gt ? j0 + 4 * (threadIdx.x + kHsThreads * g) + u : bestj;
-            any_hit |= v[g][u] > ta;
         }
-    if (__any_sync(0xFFFFFFFFu, any_hit)) {
+    if (__any_sync(0xFFFFFFFFu, best > ta)) {
 #pragma unroll
         for (int g = 0; g < kK1Vec; ++g)
 #pragma unroll
@@ -163,11 +161,15 @@ __device__ __forceinline__ void hs_row_body(const float *const (&rp)[KL], const 
         }
         terms[u] = t;
     }
+    // Term l of fundamental jbase + 32 u sits at p[l] + 32 l u: one 64-bit address per term, then
+    // constant offsets.
+    const float *p[KL];
+#pragma unroll
+    for (int l = 1; l <= KL; ++l) p[l - 1] = rp[l - 1] + (size_t)l * (unsigned)jbase;
 #pragma unroll
     for (int u = 0; u < kJpt; ++u)
 #pragma unroll
-        for (int l = 1; l <= KL; ++l)
-            v[u][l - 1] = (FULL || l <= terms[u]) ? __ldg(rp[l - 1] + (size_t)l * (jbase + 32 * u)) : 0.0f;
+        for (int l = 1; l <= KL; ++l) v[u][l - 1] = (FULL || l <= terms[u]) ? __ldg(p[l - 1] + 32 * l * u) : 0.0f;
     // HP_k = HP_{k-1} + P[c + k i][k j] in float32, k = 1, 2, ..., with each thread's best point per plane.
     float best[KL];
     int bestj[KL];
@@ -176,7 +178,6 @@ __device__ __forceinline__ void hs_row_body(const float *const (&rp)[KL], const 
         best[l] = -1.0f;
         bestj[l] = 0;
     }
-    bool any_hit = false;
 #pragma unroll
     for (int u = 0; u < kJpt; ++u) {
         const int j = jbase + 32 * u;
@@ -184,13 +185,15 @@ __device__ __forceinline__ void hs_row_body(const float *const (&rp)[KL], const 
 #pragma unroll
         for (int l = 1; l <= KL; ++l) {
             hp = (l == 1) ? v[u][0] : __fadd_rn(hp, v[u][l - 1]);
-            const bool ok = FULL || l <= terms[u];
-            const bool gt = ok && hp > best[l - 1];
+            const bool gt = (FULL || l <= terms[u]) && hp > best[l - 1];
             best[l - 1] = gt ? hp : best[l - 1];
             bestj[l - 1] = gt ? j : bestj[l - 1];
-            any_hit |= ok && hp > ta[l - 1];
         }
     }
+    // A threshold is crossed in this thread iff some plane's best value crosses it.
+    bool any_hit = false;
+#pragma unroll
+    for (int l = 0; l < KL; ++l) any_hit |= best[l] > ta[l];
     // Rare path: recompute the same sums and compact the crossings.
     if (__any_sync(0xFFFFFFFFu, any_hit)) {
 #pragma unroll
