@@ -9,10 +9,11 @@
 //   fdas_hs_reset    zeroes the per-plane crossing counters and peak keys in the workspace.
 //   fdas_hs_k1/kl<K> one launch per group of rows that take part in the same number K of planes
 //                    (K = min(n_harm, floor(c/|i|))), each compiled for exactly K terms; grid
-//                    (column blocks of 1024 fundamentals, rows of the group). Rows with one plane
-//                    stream 16-byte loads, 4096 columns per CTA. The others issue every strided
-//                    gather P[c + l i][l j] of a thread's 4 fundamentals before summing, through
-//                    the read-only path. Crossings are rare and take a separate path: a ballot, one
+//                    (column blocks, rows of the group). Rows with one plane stream 16-byte loads,
+//                    4096 columns per CTA. The others take 8 chunks of 1024 columns per CTA; in each
+//                    chunk a thread issues every strided gather P[c + l i][l j] of its 4
+//                    fundamentals before summing, through the read-only path, and warps whose
+//                    columns all have the same number of terms skip the per-element domain test. Crossings are rare and take a separate path: a ballot, one
 //                    atomicAdd per warp, and a prefix popcount for each lane's slot. Each candidate
 //                    is one 64-bit key whose ascending order is the canonical order (power desc,
 //                    i asc, j asc). The loudest point of every plane comes from warp reductions
@@ -48,8 +49,6 @@ __global__ void fdas_hs_reset(unsigned long long *counters, unsigned long long *
 }
 
 constexpr int kHsWarps = kHsThreads / 32;
-constexpr int kJpt = 4;                          // fundamentals per thread
-constexpr int kColsPerBlock = kHsThreads * kJpt;  // 1024 fundamental columns per CTA
 
 // Warp-wide candidate compaction: one ballot, one atomicAdd per warp, a prefix popcount per lane.
 __device__ __forceinline__ void emit(bool hit, float hp, int row, unsigned j, int plane_k, int lane,
@@ -138,77 +137,74 @@ __device__ __forceinline__ void hs_row_k1(const float *__restrict__ prow, int n,
     block_peaks<1>(key, peaks);
 }
 
-// Rows with KL >= 2 planes: lane L of warp w handles j = j0 + 32 kJpt w + L + 32 u. Every gather of a
-// warp is one coalesced stride-l access along a plane row. FULL: every fundamental of the warp has
-// all KL terms (l j <= n-1 for l <= KL), which holds everywhere except near the domain edges.
-template <int KL, bool FULL>
-__device__ __forceinline__ void hs_row_body(const float *const (&rp)[KL], const float (&ta)[KL], int n, int row,
-                                            int jbase, int lane, unsigned long long *raw,
-                                            unsigned long long *counters, unsigned long long (&key)[KL]) {
-    float v[kJpt][KL];
-    int terms[kJpt];
+// Number of terms of fundamental column j: the planes l <= KL with l j <= n-1 (0 for j >= n).
+template <int KL>
+__device__ __forceinline__ int term_count(int j, int n) {
+    if (j >= n) return 0;
+    if (j == 0) return KL;
+    const int t = (n - 1) / j;
+    return t < KL ? t : KL;
+}
+
+// Rows with KL >= 2 planes. A CTA covers kChunks chunks of 256 J fundamental columns (J = jpt<KL>()); in a
+// chunk, lane L of warp w handles j = jc + 32 J w + L + 32 u, u < J, so every gather of a warp is one coalesced stride-l
+// access along a plane row. The per-plane best points accumulate over the chunks, and the peak
+// reductions, the block merge and the atomics run once per CTA. UNIFORM: every fundamental of the
+// warp's chunk has the same number T of terms, which holds for all warps but those straddling a
+// boundary j = (n-1)/l.
+constexpr int kChunks = 8;
+// Fundamentals per thread and chunk: fewer for many planes, to keep the gathers in registers.
+template <int KL>
+__host__ __device__ constexpr int jpt() { return KL <= 9 ? 4 : 2; }
+
+template <int KL, bool UNIFORM>
+__device__ __forceinline__ void hs_chunk(const float *const (&rp)[KL], const float (&ta)[KL], int n, int row,
+                                         int jbase, int T, int lane, unsigned long long *raw,
+                                         unsigned long long *counters, float (&best)[KL], int (&bestj)[KL]) {
+    float v[jpt<KL>()][KL];
+    int terms[jpt<KL>()];
 #pragma unroll
-    for (int u = 0; u < kJpt; ++u) {
-        const int j = jbase + 32 * u;
-        int t = KL;
-        if (!FULL) {
-            t = 0;
-            if (j < n) {
-#pragma unroll
-                for (int l = 1; l <= KL; ++l)
-                    if ((long long)l * j <= (long long)(n - 1)) t = l;
-            }
-        }
-        terms[u] = t;
-    }
+    for (int u = 0; u < jpt<KL>(); ++u) terms[u] = UNIFORM ? T : term_count<KL>(jbase + 32 * u, n);
     // Term l of fundamental jbase + 32 u sits at p[l] + 32 l u: one 64-bit address per term, then
     // constant offsets.
     const float *p[KL];
 #pragma unroll
     for (int l = 1; l <= KL; ++l) p[l - 1] = rp[l - 1] + (size_t)l * (unsigned)jbase;
 #pragma unroll
-    for (int u = 0; u < kJpt; ++u)
+    for (int l = 1; l <= KL; ++l) {
+        if (UNIFORM && l > T) break;  // warp-uniform
 #pragma unroll
-        for (int l = 1; l <= KL; ++l) v[u][l - 1] = (FULL || l <= terms[u]) ? __ldg(p[l - 1] + 32 * l * u) : 0.0f;
-    // HP_k = HP_{k-1} + P[c + k i][k j] in float32, k = 1, 2, ..., with each thread's best point per plane.
-    float best[KL];
-    int bestj[KL];
-#pragma unroll
-    for (int l = 0; l < KL; ++l) {
-        best[l] = -1.0f;
-        bestj[l] = 0;
+        for (int u = 0; u < jpt<KL>(); ++u) v[u][l - 1] = (UNIFORM || l <= terms[u]) ? __ldg(p[l - 1] + 32 * l * u) : 0.0f;
     }
+    bool any_hit = false;
 #pragma unroll
-    for (int u = 0; u < kJpt; ++u) {
+    for (int u = 0; u < jpt<KL>(); ++u) {
         const int j = jbase + 32 * u;
         float hp = 0.0f;
 #pragma unroll
         for (int l = 1; l <= KL; ++l) {
+            if (UNIFORM && l > T) break;
             hp = (l == 1) ? v[u][0] : __fadd_rn(hp, v[u][l - 1]);
-            const bool gt = (FULL || l <= terms[u]) && hp > best[l - 1];
+            const bool ok = UNIFORM || l <= terms[u];
+            const bool gt = ok && hp > best[l - 1];
             best[l - 1] = gt ? hp : best[l - 1];
             bestj[l - 1] = gt ? j : bestj[l - 1];
+            any_hit |= ok && hp > ta[l - 1];
         }
     }
-    // A threshold is crossed in this thread iff some plane's best value crosses it.
-    bool any_hit = false;
+    if (__any_sync(0xFFFFFFFFu, any_hit)) {  // rare: recompute the same sums and compact the crossings
 #pragma unroll
-    for (int l = 0; l < KL; ++l) any_hit |= best[l] > ta[l];
-    // Rare path: recompute the same sums and compact the crossings.
-    if (__any_sync(0xFFFFFFFFu, any_hit)) {
-#pragma unroll
-        for (int u = 0; u < kJpt; ++u) {
+        for (int u = 0; u < jpt<KL>(); ++u) {
             const unsigned j = (unsigned)(jbase + 32 * u);
             float hp = 0.0f;
 #pragma unroll
             for (int l = 1; l <= KL; ++l) {
+                if (UNIFORM && l > T) break;  // warp-uniform; terms past T were not loaded
                 hp = (l == 1) ? v[u][0] : __fadd_rn(hp, v[u][l - 1]);
-                emit((FULL || l <= terms[u]) && hp > ta[l - 1], hp, row, j, l, lane, counters, raw);
+                emit(l <= terms[u] && hp > ta[l - 1], hp, row, j, l, lane, counters, raw);
             }
         }
     }
-#pragma unroll
-    for (int l = 0; l < KL; ++l) key[l] = warp_peak_key(best[l], bestj[l], row);
 }
 
 template <int KL>
@@ -217,7 +213,6 @@ __device__ __forceinline__ void hs_row(const float *__restrict__ plane, int n, s
                                        unsigned long long *counters, unsigned long long *peaks) {
     const int row = c + i;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int jw = j0 + warp * (32 * kJpt);
     const float *rp[KL];
     float ta[KL];
 #pragma unroll
@@ -225,11 +220,25 @@ __device__ __forceinline__ void hs_row(const float *__restrict__ plane, int n, s
         rp[l - 1] = plane + (size_t)(c + l * i) * ld;
         ta[l - 1] = ((mask >> (l - 1)) & 1u) ? __ldg(&thresh[(l - 1) * n_temp + row]) : __int_as_float(0x7f800000);
     }
+    float best[KL];
+    int bestj[KL];
+#pragma unroll
+    for (int l = 0; l < KL; ++l) {
+        best[l] = -1.0f;
+        bestj[l] = 0;
+    }
+    for (int ch = 0; ch < kChunks; ++ch) {
+        const int jw = j0 + ch * (kHsThreads * jpt<KL>()) + warp * (32 * jpt<KL>());
+        if (jw >= n) break;  // warp-uniform
+        const int t_first = term_count<KL>(jw, n), t_last = term_count<KL>(jw + 32 * jpt<KL>() - 1, n);
+        if (t_first == t_last)  // warp-uniform
+            hs_chunk<KL, true>(rp, ta, n, row, jw + lane, t_last, lane, raw, counters, best, bestj);
+        else
+            hs_chunk<KL, false>(rp, ta, n, row, jw + lane, 0, lane, raw, counters, best, bestj);
+    }
     unsigned long long key[KL];
-    if ((long long)(jw + 32 * kJpt - 1) * KL <= (long long)(n - 1))  // warp-uniform
-        hs_row_body<KL, true>(rp, ta, n, row, jw + lane, lane, raw, counters, key);
-    else
-        hs_row_body<KL, false>(rp, ta, n, row, jw + lane, lane, raw, counters, key);
+#pragma unroll
+    for (int l = 0; l < KL; ++l) key[l] = warp_peak_key(best[l], bestj[l], row);
     block_peaks<KL>(key, peaks);
 }
 
@@ -263,8 +272,8 @@ __global__ void __launch_bounds__(kHsThreads, KL <= 3 ? 4 : 2)
                unsigned mask, int lo, unsigned long long *__restrict__ raw, unsigned long long *counters,
                unsigned long long *peaks) {
     const int c = (n_temp - 1) / 2;
-    hs_row<KL>(plane, n, ld, thresh, n_temp, mask, c, group_row_offset(blockIdx.y, lo), blockIdx.x * kColsPerBlock,
-               raw, counters, peaks);
+    hs_row<KL>(plane, n, ld, thresh, n_temp, mask, c, group_row_offset(blockIdx.y, lo),
+               blockIdx.x * (kChunks * kHsThreads * jpt<KL>()), raw, counters, peaks);
 }
 
 using HsKernel = void (*)(const float *, int, size_t, const float *, int, unsigned, int, unsigned long long *,
@@ -360,8 +369,9 @@ cudaError_t launch_harmonic(const fdas_params &p, const float *plane, size_t n, 
     // Rows grouped by their number of planes klast: klast = n_harm for |i| <= c / n_harm, and
     // klast = K < n_harm for c/(K+1) < |i| <= c/K.
     const int c = (p.n_temp - 1) / 2;
-    const unsigned gx = (unsigned)((n + kColsPerBlock - 1) / kColsPerBlock);
     for (int K = p.n_harm; K >= 1; --K) {
+        const int per = kChunks * kHsThreads * (K <= 9 ? jpt<9>() : jpt<10>());  // columns per CTA
+        const unsigned gx = (unsigned)((n + per - 1) / per);
         const int lo = (K == p.n_harm) ? 0 : c / (K + 1) + 1;
         const int hi = c / K;
         if (hi < lo) continue;
