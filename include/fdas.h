@@ -54,6 +54,7 @@ typedef int fdas_status;
 #define FDAS_RAW_CAP 16384
 #define FDAS_MAX_CAND_CAP 4096
 #define FDAS_MAX_HARM 16
+#define FDAS_MAX_BATCH 256
 
 /*
  * Search parameters (the paper's parameter table in Sec. 2, "FDAS Module Parameters").
@@ -251,6 +252,58 @@ fdas_status fdas_search_host(const fdas_params *p, const void *h_spec, size_t n,
 fdas_status fdas_harmonic_sum_noalloc(const fdas_params *p, const float *d_plane, size_t n, size_t ld,
                                       const float *d_thresh, fdas_cand *d_cands, uint32_t *d_counts,
                                       fdas_cand *d_peaks, fdas_stream_t stream);
+
+/* ---- Batched form: many spectra (DM trials) of uneven length in one launch per stage ---------- */
+
+/* One spectrum of a batch, with its own outputs (shapes as in fdas_search). */
+typedef struct {
+    const void *d_spec; /* complex64[n] */
+    uint64_t n;         /* 1..FDAS_MAX_N */
+    float *d_plane;     /* float32[n_temp][ld] */
+    uint64_t ld;        /* >= n */
+    fdas_cand *d_cands; /* [n_harm][cand_cap] */
+    uint32_t *d_counts; /* [n_harm] */
+    fdas_cand *d_peaks; /* [n_harm] or NULL */
+} fdas_batch_item;
+
+/* Workspace of fdas_search_batch for count spectra: one harmonic-sum workspace per spectrum
+ * (fdas_workspace_bytes rounded up to 256 bytes each). Returns 0 for invalid arguments. */
+size_t fdas_batch_workspace_bytes(const fdas_params *p, int count);
+
+/*
+ * fdas_search on count (1..FDAS_MAX_BATCH) spectra of any lengths, with one launch per stage for the
+ * whole batch rather than per spectrum. The paper pipelines a stream of input arrays through one
+ * device (Sec. 3.3) or spreads them over devices (Sec. 3.5, "single bitstream, multiple inputs").
+ * Here one GPU takes them all at once:
+ *   - a persistent convolution kernel whose CTAs loop over every (spectrum, segment) work item;
+ *   - the harmonic sum of every spectrum: one launch per group of rows, then one finalize launch.
+ * Results are those of fdas_search on each spectrum alone, bit for bit. The per-spectrum tables are
+ * kernel parameters, so the call enqueues kernels only: no allocation, copy or synchronisation. It
+ * can therefore be captured in a CUDA graph. cfg (NULL = defaults) shapes the convolution launch; a
+ * persistent grid always has ctas_per_sm (0 means 3) CTAs per SM.
+ */
+fdas_status fdas_search_batch(const fdas_params *p, const fdas_batch_item *items, int count, const void *d_tmpl,
+                              const float *d_thresh, void *d_ws, size_t ws_bytes, const fdas_launch_config *cfg,
+                              fdas_stream_t stream);
+
+/*
+ * A batch plan: fdas_search_batch with fixed buffers, replayed as a CUDA graph.
+ *   create  checks and copies the item list (the buffers themselves are not copied and must stay valid).
+ *   tune    times the candidate convolution launch shapes (ctas_per_sm in {0, 2}, templates_per_item in
+ *           {0, 43, 29, 17}) on the plan's own spectra with CUDA events, keeps the fastest, and returns
+ *           it with its convolution time per batch. It waits on stream.
+ *   launch  enqueues the batch on stream. The first launch (and the first after tune) captures the
+ *           launches into a CUDA graph on a private stream; later launches replay that graph.
+ *   destroy frees the plan and its graph.
+ * A plan holds host memory and a CUDA graph; it allocates no device memory.
+ */
+typedef struct fdas_batch_plan fdas_batch_plan;
+fdas_status fdas_batch_plan_create(const fdas_params *p, const fdas_batch_item *items, int count, const void *d_tmpl,
+                                   const float *d_thresh, void *d_ws, size_t ws_bytes, fdas_batch_plan **plan);
+fdas_status fdas_batch_plan_tune(fdas_batch_plan *plan, fdas_stream_t stream, fdas_launch_config *chosen,
+                                 float *ms_per_batch);
+fdas_status fdas_batch_plan_launch(fdas_batch_plan *plan, fdas_stream_t stream);
+void fdas_batch_plan_destroy(fdas_batch_plan *plan);
 
 #ifdef __cplusplus
 }

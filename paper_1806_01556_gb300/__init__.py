@@ -37,6 +37,10 @@ __all__ = [
     "fdas_harmonic_sum_noalloc",
     "decode_cands",
     "Searcher",
+    "fdas_batch_workspace_bytes",
+    "fdas_search_batch",
+    "BatchPlan",
+    "Batch",
 ]
 
 # Host view of fdas_cand (12 bytes): power, j, i, k, pad.
@@ -180,6 +184,112 @@ def fdas_harmonic_sum_noalloc(p: Params, d_plane, n, ld, d_thresh, d_cands, d_co
         ),
         "fdas_harmonic_sum_noalloc",
     )
+
+
+def fdas_batch_workspace_bytes(p: Params, count: int) -> int:
+    return lib().fdas_batch_workspace_bytes(C.byref(p.c()), count)
+
+
+def _items(entries) -> "C.Array":
+    """entries: (d_spec, n, d_plane, ld, d_cands, d_counts, d_peaks) tuples -> fdas_batch_item[count]."""
+    arr = (_lib.fdas_batch_item * len(entries))()
+    for k, (spec, n, plane, ld, cands, counts, peaks) in enumerate(entries):
+        arr[k] = _lib.fdas_batch_item(_ptr(spec).value, n, _ptr(plane).value, ld, _ptr(cands).value,
+                                      _ptr(counts).value, _ptr(peaks).value)
+    return arr
+
+
+def fdas_search_batch(p: Params, entries, d_tmpl, d_thresh, d_ws, ws_bytes, ctas_per_sm=0, templates_per_item=0,
+                      stream=None) -> None:
+    arr = _items(entries)
+    cfg = _lib.fdas_launch_config(ctas_per_sm, templates_per_item)
+    _check(
+        lib().fdas_search_batch(C.byref(p.c()), C.cast(arr, C.c_void_p), len(entries), _ptr(d_tmpl), _ptr(d_thresh),
+                                _ptr(d_ws), ws_bytes, C.byref(cfg), _stream(stream)),
+        "fdas_search_batch",
+    )
+
+
+class BatchPlan:
+    """fdas_batch_plan: a batch with fixed buffers, replayed as a CUDA graph; tune() picks the launch shape."""
+
+    def __init__(self, p: Params, entries, d_tmpl, d_thresh, d_ws, ws_bytes):
+        arr = _items(entries)
+        self._h = C.c_void_p()
+        self._keep = (entries, d_tmpl, d_thresh, d_ws)
+        _check(
+            lib().fdas_batch_plan_create(C.byref(p.c()), C.cast(arr, C.c_void_p), len(entries), _ptr(d_tmpl),
+                                         _ptr(d_thresh), _ptr(d_ws), ws_bytes, C.byref(self._h)),
+            "fdas_batch_plan_create",
+        )
+
+    def tune(self, stream=None):
+        cfg = _lib.fdas_launch_config()
+        ms = C.c_float()
+        _check(lib().fdas_batch_plan_tune(self._h, _stream(stream), C.byref(cfg), C.byref(ms)), "fdas_batch_plan_tune")
+        return (cfg.ctas_per_sm, cfg.templates_per_item), ms.value
+
+    def launch(self, stream=None) -> None:
+        _check(lib().fdas_batch_plan_launch(self._h, _stream(stream)), "fdas_batch_plan_launch")
+
+    def close(self) -> None:
+        if self._h:
+            lib().fdas_batch_plan_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Device buffers for a batch of spectra of the given lengths, allocated once with torch."""
+
+    def __init__(self, params: Params, lengths, thresh: np.ndarray | None = None, device: str = "cuda:0"):
+        import torch
+
+        st = fdas_check_params(params)
+        if st != _lib.FDAS_OK:
+            raise FdasError(st, "params")
+        self.p = params
+        self.lengths = [int(n) for n in lengths]
+        self.device = torch.device(device)
+        u8 = dict(dtype=torch.uint8, device=self.device)
+        self.tmpl = torch.empty(fdas_templates_bytes(params), **u8)
+        ta = fdas_default_thresholds(params) if thresh is None else np.ascontiguousarray(thresh, dtype=np.float32)
+        self.thresh = torch.from_numpy(ta).to(self.device)
+        self.ws_bytes = fdas_batch_workspace_bytes(params, len(self.lengths))
+        self.ws = torch.empty(self.ws_bytes, **u8)
+        nrec = params.n_harm * params.cand_cap * CAND_DTYPE.itemsize
+        self.specs, self.planes, self.cands, self.counts, self.peaks, self.ld = [], [], [], [], [], []
+        for n in self.lengths:
+            ld = round_up(n, 64)
+            self.ld.append(ld)
+            self.specs.append(torch.empty(n, dtype=torch.complex64, device=self.device))
+            self.planes.append(torch.empty((params.n_temp, ld), dtype=torch.float32, device=self.device))
+            self.cands.append(torch.empty(nrec, **u8))
+            self.counts.append(torch.empty(params.n_harm, dtype=torch.int32, device=self.device))
+            self.peaks.append(torch.empty(params.n_harm * CAND_DTYPE.itemsize, **u8))
+        with torch.cuda.device(self.device):
+            fdas_make_templates(params, self.tmpl)
+
+    def entries(self):
+        return [(self.specs[b], n, self.planes[b], self.ld[b], self.cands[b], self.counts[b], self.peaks[b])
+                for b, n in enumerate(self.lengths)]
+
+    def search(self, ctas_per_sm=0, templates_per_item=0, stream=None) -> None:
+        fdas_search_batch(self.p, self.entries(), self.tmpl, self.thresh, self.ws, self.ws_bytes, ctas_per_sm,
+                          templates_per_item, stream)
+
+    def plan(self) -> BatchPlan:
+        return BatchPlan(self.p, self.entries(), self.tmpl, self.thresh, self.ws, self.ws_bytes)
+
+    def results(self, b: int):
+        counts = self.counts[b].cpu().numpy().astype(np.uint32)
+        return (decode_cands(self.cands[b].cpu().numpy(), counts, self.p.cand_cap), counts,
+                self.peaks[b].cpu().numpy().view(CAND_DTYPE).copy())
 
 
 def decode_cands(raw: np.ndarray, counts: np.ndarray, cand_cap: int) -> list[np.ndarray]:

@@ -23,6 +23,7 @@ FDAS_RAW_CAP = 16384
 FDAS_MAX_CAND_CAP = 4096
 FDAS_MAX_HARM = 16
 FDAS_NOALLOC_SCRATCH_BYTES = 8 * 8 * (FDAS_RAW_CAP + 4)
+FDAS_MAX_BATCH = 256
 
 
 class fdas_params(C.Structure):
@@ -41,6 +42,18 @@ class fdas_params(C.Structure):
 
 class fdas_launch_config(C.Structure):
     _fields_ = [("ctas_per_sm", C.c_int32), ("templates_per_item", C.c_int32)]
+
+
+class fdas_batch_item(C.Structure):
+    _fields_ = [
+        ("d_spec", C.c_void_p),
+        ("n", C.c_uint64),
+        ("d_plane", C.c_void_p),
+        ("ld", C.c_uint64),
+        ("d_cands", C.c_void_p),
+        ("d_counts", C.c_void_p),
+        ("d_peaks", C.c_void_p),
+    ]
 
 
 class fdas_cand(C.Structure):
@@ -67,6 +80,12 @@ SIGNATURES = {
     "fdas_search": (C.c_int, [P, VP, SZ, VP, VP, SZ, VP, VP, VP, VP, VP, SZ, VP]),
     "fdas_search_host": (C.c_int, [P, VP, SZ, VP, VP, VP, SZ, VP, VP, VP, VP, VP, VP, VP, VP, SZ, VP]),
     "fdas_harmonic_sum_noalloc": (C.c_int, [P, VP, SZ, SZ, VP, VP, VP, VP, VP]),
+    "fdas_batch_workspace_bytes": (SZ, [P, C.c_int]),
+    "fdas_search_batch": (C.c_int, [P, VP, C.c_int, VP, VP, VP, SZ, VP, VP]),
+    "fdas_batch_plan_create": (C.c_int, [P, VP, C.c_int, VP, VP, VP, SZ, C.POINTER(C.c_void_p)]),
+    "fdas_batch_plan_tune": (C.c_int, [VP, VP, VP, C.POINTER(C.c_float)]),
+    "fdas_batch_plan_launch": (C.c_int, [VP, VP]),
+    "fdas_batch_plan_destroy": (None, [VP]),
 }
 
 _lib = None

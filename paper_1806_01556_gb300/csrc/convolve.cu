@@ -175,9 +175,60 @@ __device__ __forceinline__ void stage_template(unsigned sdst, const float2 *gsrc
 
 constexpr size_t kSmemBytes = (2 * kPadded + 2 * kF) * sizeof(float2);  // two exchange + two template buffers
 
+// One work item: segment s of one spectrum with templates [t0, t1).
+struct Item {
+    const float2 *spec;
+    float *plane;
+    size_t ld;
+    int n;
+    int s;
+    int t0;
+    int t1;
+};
+
+// Work items of a single spectrum: item = s * n_tchunk + chunk.
+struct SingleJobs {
+    const float2 *spec;
+    float *plane;
+    size_t ld;
+    int n;
+    int n_seg;
+    int t_chunk;
+    int n_tchunk;
+    int n_temp;
+    __device__ int total() const { return n_seg * n_tchunk; }
+    __device__ Item get(int item) const {
+        const int s = item / n_tchunk;
+        const int t0 = (item - s * n_tchunk) * t_chunk;
+        return Item{spec, plane, ld, n, s, t0, min(t0 + t_chunk, n_temp)};
+    }
+};
+
+// Work items of a batch (a kernel parameter): the items of spectrum b are
+// [job[b].item0, job[b].item0 + n_seg_b * n_tchunk).
+struct BatchJobs {
+    ConvBatch batch;
+    int t_chunk;
+    int n_tchunk;
+    int n_temp;
+    __device__ int total() const { return batch.total_items; }
+    __device__ Item get(int item) const {
+        int lo = 0, hi = batch.count - 1;  // last job with item0 <= item
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (batch.job[mid].item0 <= item) lo = mid; else hi = mid - 1;
+        }
+        const ConvJob &J = batch.job[lo];
+        const int local = item - J.item0;
+        const int s = local / n_tchunk;
+        const int t0 = (local - s * n_tchunk) * t_chunk;
+        return Item{J.spec, J.plane, (size_t)J.ld, J.n, s, t0, min(t0 + t_chunk, n_temp)};
+    }
+};
+
+template <class Jobs>
 __global__ void __launch_bounds__(kThreads, 3)
-    fdas_ols_fp32(const float2 *__restrict__ spec, int n, const float2 *__restrict__ tmpl, int n_temp, int h, int keep,
-                  float *__restrict__ plane, size_t ld, int n_seg, int t_chunk, int n_tchunk) {
+    fdas_ols_fp32(Jobs jobs, const float2 *__restrict__ tmpl, int n_temp, int h, int keep) {
     extern __shared__ float2 smem[];
     float2 *buf0 = smem;
     float2 *buf1 = smem + kPadded;
@@ -208,14 +259,14 @@ __global__ void __launch_bounds__(kThreads, 3)
             if (m >= h && m < h + keep) keep_mask |= 1u << (8 * hh + r);
         }
     const float scale = 1.0f / kF;
-    const int n_items = n_seg * n_tchunk;
+    const int n_items = jobs.total();
 
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-        const int s = item / n_tchunk;
-        const int t0 = (item - s * n_tchunk) * t_chunk;
-        const int t1 = min(t0 + t_chunk, n_temp);
-        const int origin = s * keep - h;               // input index of segment point 0
-        const int col0 = s * keep - h;                 // column of segment time index 0
+        const Item it = jobs.get(item);
+        const int n = it.n, s = it.s, t0 = it.t0, t1 = it.t1;
+        const float2 *__restrict__ spec = it.spec;
+        const int origin = s * keep - h;  // input index of segment point 0
+        const int col0 = s * keep - h;    // column of segment time index 0
         // Outputs this thread stores for this segment: valid (keep_mask) and inside the spectrum.
         unsigned smask = keep_mask;
         if ((s + 1) * keep > n) {
@@ -259,7 +310,7 @@ __global__ void __launch_bounds__(kThreads, 3)
 #pragma unroll
             for (int q = 0; q < 16; ++q) v[q] = cmul(W[q], T[128 * q]);
             fft_passes_12<true>(v, buf0, buf1, tw2, tid);
-            float *row = plane + (size_t)t * ld;
+            float *row = it.plane + (size_t)t * it.ld;
 #pragma unroll
             for (int hh = 0; hh < 2; ++hh) {
                 float2 u[8];
@@ -275,25 +326,60 @@ __global__ void __launch_bounds__(kThreads, 3)
 
 }  // namespace
 
+static void chunking(const Geometry &g, int templates_per_item, int *t_chunk, int *n_tchunk) {
+    *t_chunk = (templates_per_item > 0 && templates_per_item < g.n_temp) ? templates_per_item : g.n_temp;
+    *n_tchunk = (g.n_temp + *t_chunk - 1) / *t_chunk;
+}
+
+static cudaError_t persistent_grid(int n_items, int ctas_per_sm, int *grid) {
+    *grid = n_items;
+    if (ctas_per_sm <= 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    *grid = n_items < ctas_per_sm * sms ? n_items : ctas_per_sm * sms;
+    return cudaSuccess;
+}
+
 cudaError_t launch_convolve_fp32(const Geometry &g, const float2 *spec, size_t n, const float2 *tmpl, float *plane,
                                  size_t ld, int ctas_per_sm, int templates_per_item, cudaStream_t s) {
-    const int n_seg = (int)((n + g.keep - 1) / g.keep);
     // A work item is one segment with t_chunk templates; the segment's forward FFT is done once per item.
-    const int t_chunk = (templates_per_item > 0 && templates_per_item < g.n_temp) ? templates_per_item : g.n_temp;
-    const int n_tchunk = (g.n_temp + t_chunk - 1) / t_chunk;
-    const int n_items = n_seg * n_tchunk;
-    int grid = n_items;
-    if (ctas_per_sm > 0) {
-        int dev = 0, sms = 0;
-        cudaError_t e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) return e;
-        grid = n_items < ctas_per_sm * sms ? n_items : ctas_per_sm * sms;
-    }
-    cudaError_t e = cudaFuncSetAttribute(fdas_ols_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    SingleJobs jobs;
+    jobs.spec = spec;
+    jobs.plane = plane;
+    jobs.ld = ld;
+    jobs.n = (int)n;
+    jobs.n_seg = (int)((n + g.keep - 1) / g.keep);
+    jobs.n_temp = g.n_temp;
+    chunking(g, templates_per_item, &jobs.t_chunk, &jobs.n_tchunk);
+    int grid = 0;
+    cudaError_t e = persistent_grid(jobs.n_seg * jobs.n_tchunk, ctas_per_sm, &grid);
     if (e != cudaSuccess) return e;
-    fdas_ols_fp32<<<grid, kThreads, kSmemBytes, s>>>(spec, (int)n, tmpl, g.n_temp, g.h, g.keep, plane, ld, n_seg,
-                                                      t_chunk, n_tchunk);
+    e = cudaFuncSetAttribute(fdas_ols_fp32<SingleJobs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    if (e != cudaSuccess) return e;
+    fdas_ols_fp32<<<grid, kThreads, kSmemBytes, s>>>(jobs, tmpl, g.n_temp, g.h, g.keep);
+    return cudaGetLastError();
+}
+
+cudaError_t prepare_convolve_batch() {
+    return cudaFuncSetAttribute(fdas_ols_fp32<BatchJobs>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kSmemBytes);
+}
+
+int convolve_items(const Geometry &g, size_t n, int templates_per_item) {
+    int t_chunk, n_tchunk;
+    chunking(g, templates_per_item, &t_chunk, &n_tchunk);
+    return (int)((n + g.keep - 1) / g.keep) * n_tchunk;
+}
+
+cudaError_t launch_convolve_batch(const Geometry &g, const ConvBatch &batch, const float2 *tmpl, int grid,
+                                  int templates_per_item, cudaStream_t s) {
+    BatchJobs jobs;
+    jobs.batch = batch;
+    jobs.n_temp = g.n_temp;
+    chunking(g, templates_per_item, &jobs.t_chunk, &jobs.n_tchunk);
+    fdas_ols_fp32<<<grid, kThreads, kSmemBytes, s>>>(jobs, tmpl, g.n_temp, g.h, g.keep);
     return cudaGetLastError();
 }
 

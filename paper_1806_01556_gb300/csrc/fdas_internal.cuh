@@ -47,12 +47,59 @@ inline HsWorkspace hs_workspace(void *ws, int n_harm) {
 
 inline size_t hs_workspace_words(int n_harm) { return (size_t)n_harm * (FDAS_RAW_CAP + 4); }
 
+// Largest batch: the per-spectrum tables travel as kernel parameters (a few KB to 20 KB).
+constexpr int kMaxBatch = FDAS_MAX_BATCH;
+
+// One spectrum of a batch, as the batched convolution kernel reads it.
+struct ConvJob {
+    const float2 *spec;
+    float *plane;
+    unsigned long long ld;
+    int n;
+    int item0;  // first work item of this spectrum in the batch
+};
+struct ConvBatch {
+    int count;
+    int total_items;
+    ConvJob job[kMaxBatch];
+};
+
+// One spectrum of a batch, as the batched harmonic-sum kernels read it.
+struct HsJob {
+    const float *plane;
+    unsigned long long ld;
+    int n;
+    int blk0;   // first CTA of this spectrum in the launches of rows with K >= 2 planes
+    int blk1;   // first CTA of this spectrum in the launch of single-plane rows
+    int pad;
+    unsigned long long *counters;  // this spectrum's workspace (HsWorkspace)
+    unsigned long long *peaks;
+    unsigned long long *raw;
+    fdas_cand *cands;
+    uint32_t *counts;
+    fdas_cand *peak_out;
+};
+struct HsBatch {
+    int count;
+    HsJob job[kMaxBatch];
+};
+
 // Kernel launchers (each returns cudaGetLastError() of its launch).
 cudaError_t launch_templates(const fdas_params &p, void *d_tmpl, cudaStream_t s);
 cudaError_t launch_convolve_fp32(const Geometry &g, const float2 *spec, size_t n, const float2 *tmpl,
                                  float *plane, size_t ld, int ctas_per_sm, int templates_per_item, cudaStream_t s);
+// Batched convolution: one persistent launch over every segment of every spectrum.
+cudaError_t prepare_convolve_batch();
+int convolve_items(const Geometry &g, size_t n, int templates_per_item);
+cudaError_t launch_convolve_batch(const Geometry &g, const ConvBatch &batch, const float2 *tmpl, int grid,
+                                  int templates_per_item, cudaStream_t s);
 cudaError_t launch_harmonic(const fdas_params &p, const float *plane, size_t n, size_t ld,
                             const float *thresh, fdas_cand *cands, uint32_t *counts, fdas_cand *peaks,
                             const HsWorkspace &ws, cudaStream_t s);
+// Batched harmonic sum: reset, one launch per group of rows over every spectrum, finalize.
+void harmonic_blocks(const fdas_params &p, size_t n, int *blocks_kl, int *blocks_k1);
+cudaError_t prepare_harmonic_batch();
+cudaError_t launch_harmonic_batch(const fdas_params &p, const HsBatch &batch, int total_kl, int total_k1,
+                                  const float *thresh, cudaStream_t s);
 
 }  // namespace fdas

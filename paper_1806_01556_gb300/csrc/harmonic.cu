@@ -310,12 +310,11 @@ __device__ __forceinline__ fdas_cand decode_cand(unsigned long long key, int c, 
     return r;
 }
 
-__global__ void __launch_bounds__(kFinThreads)
-    fdas_hs_finalize(const unsigned long long *__restrict__ raw, const unsigned long long *counters,
-                     const unsigned long long *peaks, int n_temp, int cand_cap, fdas_cand *cands, uint32_t *counts,
-                     fdas_cand *peak_out) {
-    extern __shared__ unsigned long long keys[];
-    const int k = blockIdx.x + 1;
+// Counts, peak and the top cand_cap candidates of plane k, from its workspace.
+__device__ __forceinline__ void finalize_plane(int k, const unsigned long long *__restrict__ raw,
+                                               const unsigned long long *counters, const unsigned long long *peaks,
+                                               int n_temp, int cand_cap, fdas_cand *cands, uint32_t *counts,
+                                               fdas_cand *peak_out, unsigned long long *keys) {
     const int c = (n_temp - 1) / 2;
     const unsigned long long total = counters[k - 1];
     const int nr = (int)(total < FDAS_RAW_CAP ? total : FDAS_RAW_CAP);
@@ -358,6 +357,86 @@ __global__ void __launch_bounds__(kFinThreads)
     for (int x = threadIdx.x; x < nout; x += blockDim.x) cands[(size_t)(k - 1) * cand_cap + x] = decode_cand(keys[x], c, k);
 }
 
+__global__ void __launch_bounds__(kFinThreads)
+    fdas_hs_finalize(const unsigned long long *__restrict__ raw, const unsigned long long *counters,
+                     const unsigned long long *peaks, int n_temp, int cand_cap, fdas_cand *cands, uint32_t *counts,
+                     fdas_cand *peak_out) {
+    extern __shared__ unsigned long long keys[];
+    finalize_plane(blockIdx.x + 1, raw, counters, peaks, n_temp, cand_cap, cands, counts, peak_out, keys);
+}
+
+// ---- batched forms: one launch per stage for every spectrum of a batch ----------------------------
+
+// Spectrum of CTA x: the last job whose first CTA (field blk0 or blk1) is <= x.
+template <bool K1>
+__device__ __forceinline__ int job_of_block(const HsBatch &B, int x) {
+    int lo = 0, hi = B.count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        const int first = K1 ? B.job[mid].blk1 : B.job[mid].blk0;
+        if (first <= x) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void fdas_hs_reset_batch(const HsBatch B, int n_harm) {
+    const HsJob &J = B.job[blockIdx.x];
+    const int t = threadIdx.x;
+    if (t < n_harm) {
+        J.counters[t] = 0ull;
+        J.peaks[t] = 0ull;
+    }
+}
+
+__global__ void __launch_bounds__(kHsThreads, 4)
+    fdas_hs_k1_batch(const HsBatch B, const float *__restrict__ thresh, int n_temp, unsigned mask, int lo) {
+    const HsJob &J = B.job[job_of_block<true>(B, blockIdx.x)];
+    const int c = (n_temp - 1) / 2;
+    const int row = c + group_row_offset(blockIdx.y, lo);
+    const float ta = (mask & 1u) ? __ldg(&thresh[row]) : __int_as_float(0x7f800000);
+    const bool vec = (J.ld & 3) == 0 && (reinterpret_cast<uintptr_t>(J.plane) & 15) == 0;
+    hs_row_k1(J.plane + (size_t)row * J.ld, J.n, ta, row, (blockIdx.x - J.blk1) * kK1Cols, J.raw, J.counters, J.peaks,
+              vec);
+}
+
+template <int KL>
+__global__ void __launch_bounds__(kHsThreads, KL <= 3 ? 4 : 2)
+    fdas_hs_kl_batch(const HsBatch B, const float *__restrict__ thresh, int n_temp, unsigned mask, int lo) {
+    const HsJob &J = B.job[job_of_block<false>(B, blockIdx.x)];
+    const int c = (n_temp - 1) / 2;
+    hs_row<KL>(J.plane, J.n, (size_t)J.ld, thresh, n_temp, mask, c, group_row_offset(blockIdx.y, lo),
+               (blockIdx.x - J.blk0) * (kChunks * kHsThreads * jpt<KL>()), J.raw, J.counters, J.peaks);
+}
+
+__global__ void __launch_bounds__(kFinThreads) fdas_hs_finalize_batch(const HsBatch B, int n_temp, int cand_cap) {
+    extern __shared__ unsigned long long keys[];
+    const HsJob &J = B.job[blockIdx.y];
+    finalize_plane(blockIdx.x + 1, J.raw, J.counters, J.peaks, n_temp, cand_cap, J.cands, J.counts, J.peak_out, keys);
+}
+
+using HsBatchKernel = void (*)(const HsBatch, const float *, int, unsigned, int);
+
+HsBatchKernel hs_batch_kernel(int klast) {
+    switch (klast) {
+        case 1: return fdas_hs_k1_batch;
+        case 2: return fdas_hs_kl_batch<2>;
+        case 3: return fdas_hs_kl_batch<3>;
+        case 4: return fdas_hs_kl_batch<4>;
+        case 5: return fdas_hs_kl_batch<5>;
+        case 6: return fdas_hs_kl_batch<6>;
+        case 7: return fdas_hs_kl_batch<7>;
+        case 8: return fdas_hs_kl_batch<8>;
+        case 9: return fdas_hs_kl_batch<9>;
+        case 10: return fdas_hs_kl_batch<10>;
+        case 11: return fdas_hs_kl_batch<11>;
+        case 12: return fdas_hs_kl_batch<12>;
+        case 13: return fdas_hs_kl_batch<13>;
+        case 14: return fdas_hs_kl_batch<14>;
+        case 15: return fdas_hs_kl_batch<15>;
+        default: return fdas_hs_kl_batch<16>;
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_harmonic(const fdas_params &p, const float *plane, size_t n, size_t ld, const float *thresh,
@@ -387,6 +466,40 @@ cudaError_t launch_harmonic(const fdas_params &p, const float *plane, size_t n, 
     if (e != cudaSuccess) return e;
     fdas_hs_finalize<<<p.n_harm, kFinThreads, smem, s>>>(ws.raw, ws.counters, ws.peaks, p.n_temp, p.cand_cap, cands,
                                                           counts, peaks);
+    return cudaGetLastError();
+}
+
+// CTAs of one spectrum of n bins in the launches of rows with K >= 2 planes (all groups use the same
+// column width for n_harm <= 9) and in the launch of single-plane rows.
+void harmonic_blocks(const fdas_params &p, size_t n, int *blocks_kl, int *blocks_k1) {
+    const int per = kChunks * kHsThreads * (p.n_harm <= 9 ? jpt<9>() : jpt<10>());
+    *blocks_kl = (int)((n + per - 1) / per);
+    *blocks_k1 = (int)((n + kK1Cols - 1) / kK1Cols);
+}
+
+cudaError_t prepare_harmonic_batch() {
+    return cudaFuncSetAttribute(fdas_hs_finalize_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                FDAS_RAW_CAP * (int)sizeof(unsigned long long));
+}
+
+cudaError_t launch_harmonic_batch(const fdas_params &p, const HsBatch &B, int total_kl, int total_k1,
+                                  const float *thresh, cudaStream_t s) {
+    fdas_hs_reset_batch<<<B.count, 32, 0, s>>>(B, p.n_harm);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int c = (p.n_temp - 1) / 2;
+    for (int K = p.n_harm; K >= 1; --K) {
+        const int lo = (K == p.n_harm) ? 0 : c / (K + 1) + 1;
+        const int hi = c / K;
+        if (hi < lo) continue;
+        const int rows = (lo == 0) ? 2 * hi + 1 : 2 * (hi - lo + 1);
+        const unsigned gx = (unsigned)(K == 1 ? total_k1 : total_kl);
+        hs_batch_kernel(K)<<<dim3(gx, (unsigned)rows), kHsThreads, 0, s>>>(B, thresh, p.n_temp, p.harm_mask, lo);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    fdas_hs_finalize_batch<<<dim3((unsigned)p.n_harm, (unsigned)B.count), kFinThreads,
+                             FDAS_RAW_CAP * sizeof(unsigned long long), s>>>(B, p.n_temp, p.cand_cap);
     return cudaGetLastError();
 }
 

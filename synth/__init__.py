@@ -33,6 +33,7 @@ __all__ = [
     "small_workload",
     "ska_workload",
     "batch_lengths",
+    "batch_workloads",
 ]
 
 
@@ -154,3 +155,23 @@ def batch_lengths(count: int = 64, seed: int = 3, lo_log2: float = 18.0, hi_log2
     rng = np.random.default_rng(seed)
     u = rng.uniform(lo_log2, hi_log2, size=count)
     return [int(np.floor(2.0 ** v)) for v in u]
+
+
+def batch_workloads(count: int = 64, seed: int = 3, amp: float = 20.0) -> list[Workload]:
+    """Dedispersion-trial spectra of uneven length for batched runs.
+
+    Lengths are ``batch_lengths(count, seed)``. Spectrum b then draws from default_rng([seed, b]):
+    the number of tones (0..3), their mean bins (uniform in [2^10, n/8 - 2^10]) and drifts
+    (uniform in [-40, 40]), then its noise. Each tone has 8 harmonics with amplitudes amp/l.
+    """
+    out = []
+    for b, n in enumerate(batch_lengths(count, seed)):
+        rng = np.random.default_rng([seed, b])
+        k = int(rng.integers(0, 4))
+        lo, hi = 1 << 10, max((1 << 10) + 1, n // 8 - (1 << 10))
+        means = rng.integers(lo, hi, size=k, endpoint=True)
+        zs = rng.integers(-40, 40, size=k, endpoint=True)
+        noise = complex_noise(rng, n)
+        tones = [Tone(float(m), float(z), amp, 8) for m, z in zip(means, zs)]
+        out.append(_finish(f"trial{b}", n, seed, noise, tones))
+    return out

@@ -150,3 +150,32 @@ def test_python_wrappers_marshal_and_raise_on_rejected_arguments(fd):
         assert err.value.status == -1
     bad = fd.Params(n_temp=84)
     assert fd.fdas_templates_bytes(bad) == 0 and fd.fdas_workspace_bytes(bad, 10) == 0
+
+
+def test_batch_arguments_are_checked_on_the_host(fd):
+    from paper_1806_01556_gb300 import _lib
+
+    lib = fd.lib()
+    p = fd.Params().c()
+    assert fd.fdas_batch_workspace_bytes(fd.Params(), 4) == 4 * ((8 * 8 * (16384 + 4) + 255) // 256 * 256)
+    assert fd.fdas_batch_workspace_bytes(fd.Params(), 0) == 0
+    assert fd.fdas_batch_workspace_bytes(fd.Params(), 257) == 0
+    fake = 0x10000
+    good = _lib.fdas_batch_item(fake, 100, fake, 128, fake, fake, 0)
+    items = (_lib.fdas_batch_item * 2)(good, good)
+    ws = fd.fdas_batch_workspace_bytes(fd.Params(), 2)
+    vp = C.c_void_p
+    args = (vp(fake), vp(fake), vp(fake))
+    assert lib.fdas_search_batch(C.byref(p), C.cast(items, vp), 0, *args, ws, None, None) == -1
+    assert lib.fdas_search_batch(C.byref(p), C.cast(items, vp), 2, *args, ws - 1, None, None) == -3
+    items[1].n = 0
+    assert lib.fdas_search_batch(C.byref(p), C.cast(items, vp), 2, *args, ws, None, None) == -1
+    items[1].n, items[1].ld = 100, 99
+    assert lib.fdas_search_batch(C.byref(p), C.cast(items, vp), 2, *args, ws, None, None) == -1
+    items[1].ld, items[1].d_plane = 128, fake + 4
+    assert lib.fdas_search_batch(C.byref(p), C.cast(items, vp), 2, *args, ws, None, None) == -1
+    h = C.c_void_p()
+    assert lib.fdas_batch_plan_create(C.byref(p), C.cast(items, vp), 2, *args, ws, C.byref(h)) == -1
+    assert not h.value
+    assert lib.fdas_batch_plan_launch(None, None) == -1
+    lib.fdas_batch_plan_destroy(None)
