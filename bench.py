@@ -373,6 +373,68 @@ def run_batch(args):
     plan.close()
 
 
+def run_serve(args):
+    """Serving form: Poisson arrivals (mean 200 spectra/s, seed 4) of spectra of 2^19..2^22 bins, 16
+    harmonic planes, through the native request loop; throughput and p50/p99 latency."""
+    import torch
+
+    import paper_1806_01556_gb300 as fdas
+    import synth
+
+    torch.cuda.set_device(0)
+    p = fdas.Params(n_harm=16, harm_mask=0xFFFF)
+    sizes = [1 << 19, 1 << 20, 1 << 21, 1 << 22]
+    pool = {n: [torch.from_numpy(synth.ska_workload(n=n, seed=40 + k).spectrum).pin_memory() for k in range(2)]
+            for n in sizes}
+    rng = np.random.default_rng(4)
+    n_req = int(args.rate * args.duration)
+    gaps = rng.exponential(1.0 / args.rate, size=n_req)
+    which = rng.integers(0, len(sizes), size=n_req)
+    server = fdas.Server(p, device_bytes=args.serve_gb << 30, max_inflight=3)
+    # warm-up: one request of each size, not timed
+    for k, n in enumerate(sizes):
+        server.submit(pool[n][0], 10**9 + k)
+    got = 0
+    while got < len(sizes):
+        got += len(server.poll(64, wait_ms=100))
+    sampler = ClockSampler(0)
+    done = []
+    with sampler:
+        t0 = time.perf_counter()
+        t_next = t0
+        for k in range(n_req):
+            t_next += gaps[k]
+            while True:
+                now = time.perf_counter()
+                if now >= t_next:
+                    break
+                done += server.poll(256, wait_ms=0)
+                time.sleep(min(2e-4, t_next - now))
+            n = sizes[which[k]]
+            server.submit(pool[n][k % 2], k)
+        while len(done) < n_req:
+            done += server.poll(256, wait_ms=50)
+        t1 = time.perf_counter()
+    server.close()
+    lat = np.array([r["done_s"] - r["submit_s"] for r in done]) * 1e3
+    wait = np.array([r["admit_s"] - r["submit_s"] for r in done]) * 1e3
+    bins = sum(int(r["n"]) for r in done)
+    line = {
+        "metric": "FDAS serving: spectra/s and latency under Poisson arrivals", "value": n_req / (t1 - t0),
+        "unit": "spectra/s", "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"Poisson arrivals, mean {args.rate:g}/s (seed 4), {n_req} requests, lengths uniform in "
+                               "{2^19, 2^20, 2^21, 2^22}; 85 templates, 421 taps, F=2048, 16 harmonic planes",
+                   "max_inflight": 3, "arena_gb": args.serve_gb},
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "mean": float(lat.mean()), "max": float(lat.max())},
+        "queue_wait_ms": {"p50": float(np.percentile(wait, 50)), "p99": float(np.percentile(wait, 99))},
+        "fa_points_per_s": 85 * bins / (t1 - t0),
+        "failed": int(sum(1 for r in done if r["status"] != 0)),
+        "clocks": sampler.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -381,7 +443,10 @@ def main():
     ap.add_argument("--impl", default="fdas", choices=["fdas", "reference"])
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="single", choices=["single", "batch"])
+    ap.add_argument("--mode", default="single", choices=["single", "batch", "serve"])
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--duration", type=float, default=5.0)
+    ap.add_argument("--serve-gb", type=int, default=8)
     ap.add_argument("--batch", type=int, default=64)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -390,6 +455,8 @@ def main():
         run_reference(args)
     elif args.mode == "batch":
         run_batch(args)
+    elif args.mode == "serve":
+        run_serve(args)
     else:
         run_fdas(args)
 

@@ -305,6 +305,48 @@ fdas_status fdas_batch_plan_tune(fdas_batch_plan *plan, fdas_stream_t stream, fd
 fdas_status fdas_batch_plan_launch(fdas_batch_plan *plan, fdas_stream_t stream);
 void fdas_batch_plan_destroy(fdas_batch_plan *plan);
 
+/* ---- Serving form: a request loop with admission by device-memory footprint --------------------- */
+
+/* One finished request (times are seconds on the host's steady clock). */
+typedef struct {
+    uint64_t id;                       /* the caller's request id */
+    uint64_t n;                        /* spectrum length */
+    fdas_status status;                /* FDAS_OK, or the error of this request */
+    int32_t pad;
+    double submit_s;                   /* fdas_server_submit returned */
+    double admit_s;                    /* the request got a slot and its device memory, and was launched */
+    double done_s;                     /* the worker saw its results on the host */
+    uint32_t counts[FDAS_MAX_HARM];    /* as d_counts of fdas_search (first n_harm entries) */
+    fdas_cand peaks[FDAS_MAX_HARM];    /* as d_peaks of fdas_search (first n_harm entries) */
+} fdas_result;
+
+/*
+ * A request loop for a continuous stream of spectra. The paper processes a stream of input arrays
+ * through the FDAS module with double or triple buffering between its stages (Sec. 3.3, pipeline
+ * period max(t_FT, t_FOP, t_HM)). Here the buffers are device-resident and the stages of different
+ * requests overlap on the GPU.
+ *   create  takes all device memory once: the template bank, the 6-sigma thresholds and an arena of
+ *           device_bytes for requests. It starts a worker thread on the current device. Up to
+ *           max_inflight (1..16, 3 = triple buffering) requests run at once, each on its own stream.
+ *   request_bytes  the arena footprint of one request of n bins (spectrum, plane, workspace, results).
+ *   submit  queues a spectrum (host complex64[n]; pinned memory recommended; it must stay valid until
+ *           the request's result has been polled). h_cands (host fdas_cand[n_harm][cand_cap], or NULL)
+ *           receives the candidates. Requests are admitted in order as a slot and arena memory become
+ *           free; requests that arrive while others run join them on the GPU. Returns FDAS_ERR_WORKSPACE
+ *           if the request could never fit the arena.
+ *   poll    moves up to max_results finished requests into out (waiting up to wait_ms for the first).
+ *   stats   current queue length and requests in flight.
+ *   destroy waits until every submitted request has finished, then frees everything.
+ * Results are those of fdas_search on the same spectrum alone, bit for bit.
+ */
+typedef struct fdas_server fdas_server;
+fdas_status fdas_server_create(const fdas_params *p, size_t device_bytes, int max_inflight, fdas_server **server);
+size_t fdas_server_request_bytes(const fdas_params *p, uint64_t n);
+fdas_status fdas_server_submit(fdas_server *server, const void *h_spec, uint64_t n, uint64_t id, fdas_cand *h_cands);
+fdas_status fdas_server_poll(fdas_server *server, fdas_result *out, int max_results, int *n_out, int wait_ms);
+void fdas_server_stats(fdas_server *server, int *pending, int *inflight);
+void fdas_server_destroy(fdas_server *server);
+
 #ifdef __cplusplus
 }
 #endif

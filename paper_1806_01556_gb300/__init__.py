@@ -41,6 +41,7 @@ __all__ = [
     "fdas_search_batch",
     "BatchPlan",
     "Batch",
+    "Server",
 ]
 
 # Host view of fdas_cand (12 bytes): power, j, i, k, pad.
@@ -290,6 +291,64 @@ class Batch:
         counts = self.counts[b].cpu().numpy().astype(np.uint32)
         return (decode_cands(self.cands[b].cpu().numpy(), counts, self.p.cand_cap), counts,
                 self.peaks[b].cpu().numpy().view(CAND_DTYPE).copy())
+
+
+class Server:
+    """fdas_server: a request loop (native worker thread) with admission by device-memory footprint.
+
+    submit() takes a host complex64 array (keep it alive until its result is polled) and returns at
+    once; poll() returns finished requests as dicts with the candidates, counts, peaks and times.
+    """
+
+    def __init__(self, params: Params, device_bytes: int, max_inflight: int = 3):
+        self.p = params
+        self._h = C.c_void_p()
+        self._keep = {}
+        _check(lib().fdas_server_create(C.byref(params.c()), device_bytes, max_inflight, C.byref(self._h)),
+               "fdas_server_create")
+
+    @staticmethod
+    def request_bytes(params: Params, n: int) -> int:
+        return lib().fdas_server_request_bytes(C.byref(params.c()), n)
+
+    def submit(self, h_spec, request_id: int) -> None:
+        n = h_spec.numel() if hasattr(h_spec, "numel") else h_spec.size
+        cands = np.zeros(self.p.n_harm * self.p.cand_cap, dtype=CAND_DTYPE)
+        self._keep[request_id] = (h_spec, cands)
+        _check(lib().fdas_server_submit(self._h, _ptr(h_spec), n, request_id, _ptr(cands)), "fdas_server_submit")
+
+    def poll(self, max_results: int = 64, wait_ms: int = 0) -> list[dict]:
+        out = (_lib.fdas_result * max_results)()
+        got = C.c_int()
+        _check(lib().fdas_server_poll(self._h, C.cast(out, C.c_void_p), max_results, C.byref(got), wait_ms),
+               "fdas_server_poll")
+        res = []
+        for r in out[: got.value]:
+            _, cands = self._keep.pop(r.id)
+            nh = self.p.n_harm
+            counts = np.array(r.counts[:nh], dtype=np.uint32)
+            per = [cands[k * self.p.cand_cap: k * self.p.cand_cap + min(int(counts[k]), self.p.cand_cap)]
+                   for k in range(nh)]
+            peaks = np.frombuffer(bytes(r.peaks), dtype=CAND_DTYPE)[:nh].copy()
+            res.append(dict(id=r.id, n=r.n, status=r.status, submit_s=r.submit_s, admit_s=r.admit_s,
+                            done_s=r.done_s, counts=counts, cands=per, peaks=peaks))
+        return res
+
+    def stats(self):
+        pend, infl = C.c_int(), C.c_int()
+        lib().fdas_server_stats(self._h, C.byref(pend), C.byref(infl))
+        return pend.value, infl.value
+
+    def close(self) -> None:
+        if self._h:
+            lib().fdas_server_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def decode_cands(raw: np.ndarray, counts: np.ndarray, cand_cap: int) -> list[np.ndarray]:

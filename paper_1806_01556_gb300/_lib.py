@@ -60,6 +60,20 @@ class fdas_cand(C.Structure):
     _fields_ = [("power", C.c_float), ("j", C.c_uint32), ("i", C.c_int16), ("k", C.c_uint8), ("pad", C.c_uint8)]
 
 
+class fdas_result(C.Structure):
+    _fields_ = [
+        ("id", C.c_uint64),
+        ("n", C.c_uint64),
+        ("status", C.c_int32),
+        ("pad", C.c_int32),
+        ("submit_s", C.c_double),
+        ("admit_s", C.c_double),
+        ("done_s", C.c_double),
+        ("counts", C.c_uint32 * 16),
+        ("peaks", fdas_cand * 16),
+    ]
+
+
 P = C.POINTER(fdas_params)
 VP = C.c_void_p
 SZ = C.c_size_t
@@ -86,6 +100,12 @@ SIGNATURES = {
     "fdas_batch_plan_tune": (C.c_int, [VP, VP, VP, C.POINTER(C.c_float)]),
     "fdas_batch_plan_launch": (C.c_int, [VP, VP]),
     "fdas_batch_plan_destroy": (None, [VP]),
+    "fdas_server_create": (C.c_int, [P, SZ, C.c_int, C.POINTER(C.c_void_p)]),
+    "fdas_server_request_bytes": (SZ, [P, C.c_uint64]),
+    "fdas_server_submit": (C.c_int, [VP, VP, C.c_uint64, C.c_uint64, VP]),
+    "fdas_server_poll": (C.c_int, [VP, VP, C.c_int, C.POINTER(C.c_int), C.c_int]),
+    "fdas_server_stats": (None, [VP, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "fdas_server_destroy": (None, [VP]),
 }
 
 _lib = None

@@ -179,3 +179,27 @@ def test_batch_arguments_are_checked_on_the_host(fd):
     assert not h.value
     assert lib.fdas_batch_plan_launch(None, None) == -1
     lib.fdas_batch_plan_destroy(None)
+
+
+def test_server_arguments_are_checked_on_the_host(fd):
+    lib = fd.lib()
+    p = fd.Params().c()
+    h = C.c_void_p()
+    assert lib.fdas_server_create(C.byref(p), 1 << 30, 0, C.byref(h)) == -1
+    assert lib.fdas_server_create(C.byref(p), 1 << 30, 17, C.byref(h)) == -1
+    assert lib.fdas_server_create(C.byref(p), 1000, 3, C.byref(h)) == -1
+    assert lib.fdas_server_create(C.byref(p), 1 << 30, 3, None) == -1
+    assert lib.fdas_server_create(C.byref(fd.Params(n_temp=4).c()), 1 << 30, 3, C.byref(h)) == -1
+    assert not h.value
+    assert lib.fdas_server_submit(None, C.c_void_p(0x10000), 100, 1, None) == -1
+    n_out = C.c_int()
+    assert lib.fdas_server_poll(None, C.c_void_p(0x10000), 1, C.byref(n_out), 0) == -1
+    lib.fdas_server_destroy(None)
+    lib.fdas_server_stats(None, None, None)
+    # footprint: spectrum + plane (ld rounded to 64) + workspace + results, each rounded to 256 bytes
+    q = fd.Params()
+    n = 100000
+    up = lambda x: (x + 255) // 256 * 256
+    want = up(8 * n) + up(85 * ((n + 63) // 64 * 64) * 4) + up(fd.fdas_workspace_bytes(q, n)) + up(8 * 200 * 12) \
+        + up(8 * 4) + up(8 * 12)
+    assert fd.Server.request_bytes(q, n) == want
