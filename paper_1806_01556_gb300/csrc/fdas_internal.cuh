@@ -69,8 +69,8 @@ struct HsJob {
     const float *plane;
     unsigned long long ld;
     int n;
-    int blk0;   // first CTA of this spectrum in the launches of rows with K >= 2 planes
-    int blk1;   // first CTA of this spectrum in the launch of single-plane rows
+    int blk0;   // first CTA of this spectrum in harmonic-sum launches of 8192-column CTAs
+    int blk1;   // first CTA of this spectrum in harmonic-sum launches of 4096-column CTAs
     int pad;
     unsigned long long *counters;  // this spectrum's workspace (HsWorkspace)
     unsigned long long *peaks;
@@ -97,7 +97,7 @@ cudaError_t launch_harmonic(const fdas_params &p, const float *plane, size_t n, 
                             const float *thresh, fdas_cand *cands, uint32_t *counts, fdas_cand *peaks,
                             const HsWorkspace &ws, cudaStream_t s);
 // Batched harmonic sum: reset, one launch per group of rows over every spectrum, finalize.
-void harmonic_blocks(const fdas_params &p, size_t n, int *blocks_kl, int *blocks_k1);
+void harmonic_blocks(const fdas_params &p, size_t n, int *blocks_wide, int *blocks_narrow);
 cudaError_t prepare_harmonic_batch();
 cudaError_t launch_harmonic_batch(const fdas_params &p, const HsBatch &batch, int total_kl, int total_k1,
                                   const float *thresh, cudaStream_t s);

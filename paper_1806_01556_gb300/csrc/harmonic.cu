@@ -7,14 +7,16 @@
 //
 // GB300 mapping:
 //   fdas_hs_reset    zeroes the per-plane crossing counters and peak keys in the workspace.
-//   fdas_hs_k1/kl<K> one launch per group of rows that take part in the same number K of planes
-//                    (K = min(n_harm, floor(c/|i|))), each compiled for exactly K terms; grid
-//                    (column blocks, rows of the group). Rows with one plane stream 16-byte loads,
-//                    4096 columns per CTA. The others take 8 chunks of 1024 columns per CTA; in each
-//                    chunk a thread issues every strided gather P[c + l i][l j] of its 4
-//                    fundamentals before summing, through the read-only path, and warps whose
-//                    columns all have the same number of terms skip the per-element domain test. Crossings are rare and take a separate path: a ballot, one
-//                    atomicAdd per warp, and a prefix popcount for each lane's slot. Each candidate
+//   fdas_hs_k1       one launch for the single-plane rows (|i| > c/2): 16-byte streaming loads,
+//                    4096 columns per CTA.
+//   fdas_hs_kl<KL>   one launch for every row with at least two planes (|i| <= c/2), compiled for
+//                    KL >= n_harm terms; row i caps its terms at K(i) = min(n_harm, floor(c/|i|)).
+//                    A CTA takes 8 chunks of 1024 columns; in each chunk a thread issues every
+//                    strided gather P[c + l i][l j] of its 4 fundamentals before summing, through
+//                    the read-only path, and warps whose columns all have the same number of terms
+//                    skip the per-element domain test.
+//                    Crossings are rare and take a separate path: a ballot, one atomicAdd per warp,
+//                    and a prefix popcount for each lane's slot. Each candidate
 //                    is one 64-bit key whose ascending order is the canonical order (power desc,
 //                    i asc, j asc). The loudest point of every plane comes from warp reductions
 //                    (redux max of the power bits, then redux min of the column), a block merge in
@@ -159,12 +161,12 @@ __host__ __device__ constexpr int jpt() { return KL <= 9 ? 4 : 2; }
 
 template <int KL, bool UNIFORM>
 __device__ __forceinline__ void hs_chunk(const float *const (&rp)[KL], const float (&ta)[KL], int n, int row,
-                                         int jbase, int T, int lane, unsigned long long *raw,
+                                         int klast, int jbase, int T, int lane, unsigned long long *raw,
                                          unsigned long long *counters, float (&best)[KL], int (&bestj)[KL]) {
     float v[jpt<KL>()][KL];
     int terms[jpt<KL>()];
 #pragma unroll
-    for (int u = 0; u < jpt<KL>(); ++u) terms[u] = UNIFORM ? T : term_count<KL>(jbase + 32 * u, n);
+    for (int u = 0; u < jpt<KL>(); ++u) terms[u] = UNIFORM ? T : min(term_count<KL>(jbase + 32 * u, n), klast);
     // Term l of fundamental jbase + 32 u sits at p[l] + 32 l u: one 64-bit address per term, then
     // constant offsets.
     const float *p[KL];
@@ -207,18 +209,22 @@ __device__ __forceinline__ void hs_chunk(const float *const (&rp)[KL], const flo
     }
 }
 
+// Row i takes part in klast <= KL planes: rows with fewer planes than the kernel was compiled for cap
+// their term counts at klast (and never touch rows c + l i for l > klast).
 template <int KL>
 __device__ __forceinline__ void hs_row(const float *__restrict__ plane, int n, size_t ld, const float *__restrict__ thresh,
-                                       int n_temp, unsigned mask, int c, int i, int j0, unsigned long long *raw,
-                                       unsigned long long *counters, unsigned long long *peaks) {
+                                       int n_temp, unsigned mask, int c, int i, int klast, int j0,
+                                       unsigned long long *raw, unsigned long long *counters,
+                                       unsigned long long *peaks) {
     const int row = c + i;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float *rp[KL];
     float ta[KL];
 #pragma unroll
     for (int l = 1; l <= KL; ++l) {
-        rp[l - 1] = plane + (size_t)(c + l * i) * ld;
-        ta[l - 1] = ((mask >> (l - 1)) & 1u) ? __ldg(&thresh[(l - 1) * n_temp + row]) : __int_as_float(0x7f800000);
+        rp[l - 1] = plane + (size_t)(l <= klast ? c + l * i : row) * ld;
+        ta[l - 1] = (l <= klast && ((mask >> (l - 1)) & 1u)) ? __ldg(&thresh[(l - 1) * n_temp + row])
+                                                           : __int_as_float(0x7f800000);
     }
     float best[KL];
     int bestj[KL];
@@ -230,15 +236,16 @@ __device__ __forceinline__ void hs_row(const float *__restrict__ plane, int n, s
     for (int ch = 0; ch < kChunks; ++ch) {
         const int jw = j0 + ch * (kHsThreads * jpt<KL>()) + warp * (32 * jpt<KL>());
         if (jw >= n) break;  // warp-uniform
-        const int t_first = term_count<KL>(jw, n), t_last = term_count<KL>(jw + 32 * jpt<KL>() - 1, n);
+        const int t_first = min(term_count<KL>(jw, n), klast);
+        const int t_last = min(term_count<KL>(jw + 32 * jpt<KL>() - 1, n), klast);
         if (t_first == t_last)  // warp-uniform
-            hs_chunk<KL, true>(rp, ta, n, row, jw + lane, t_last, lane, raw, counters, best, bestj);
+            hs_chunk<KL, true>(rp, ta, n, row, klast, jw + lane, t_last, lane, raw, counters, best, bestj);
         else
-            hs_chunk<KL, false>(rp, ta, n, row, jw + lane, 0, lane, raw, counters, best, bestj);
+            hs_chunk<KL, false>(rp, ta, n, row, klast, jw + lane, 0, lane, raw, counters, best, bestj);
     }
     unsigned long long key[KL];
 #pragma unroll
-    for (int l = 0; l < KL; ++l) key[l] = warp_peak_key(best[l], bestj[l], row);
+    for (int l = 0; l < KL; ++l) key[l] = (l < klast) ? warp_peak_key(best[l], bestj[l], row) : 0ull;
     block_peaks<KL>(key, peaks);
 }
 
@@ -266,38 +273,53 @@ __global__ void __launch_bounds__(kHsThreads, 4)
     hs_row_k1(plane + (size_t)row * ld, n, ta, row, blockIdx.x * kK1Cols, raw, counters, peaks, vec);
 }
 
+// A group of rows with at least two planes, |i| in [lo, hi], in one launch compiled for KL terms;
+// row i caps its terms at its own klast = min(n_harm, floor(c/|i|)) <= KL.
+// Grid: (column blocks, rows of the group).
 template <int KL>
 __global__ void __launch_bounds__(kHsThreads, KL <= 3 ? 4 : 2)
     fdas_hs_kl(const float *__restrict__ plane, int n, size_t ld, const float *__restrict__ thresh, int n_temp,
-               unsigned mask, int lo, unsigned long long *__restrict__ raw, unsigned long long *counters,
+               unsigned mask, int n_harm, int lo, unsigned long long *__restrict__ raw, unsigned long long *counters,
                unsigned long long *peaks) {
     const int c = (n_temp - 1) / 2;
-    hs_row<KL>(plane, n, ld, thresh, n_temp, mask, c, group_row_offset(blockIdx.y, lo),
-               blockIdx.x * (kChunks * kHsThreads * jpt<KL>()), raw, counters, peaks);
+    const int i = group_row_offset(blockIdx.y, lo);
+    const int ai = i < 0 ? -i : i;
+    const int klast = ai == 0 ? n_harm : min(n_harm, c / ai);
+    hs_row<KL>(plane, n, ld, thresh, n_temp, mask, c, i, klast, blockIdx.x * (kChunks * kHsThreads * jpt<KL>()), raw,
+               counters, peaks);
 }
 
-using HsKernel = void (*)(const float *, int, size_t, const float *, int, unsigned, int, unsigned long long *,
+using HsKernel = void (*)(const float *, int, size_t, const float *, int, unsigned, int, int, unsigned long long *,
                           unsigned long long *, unsigned long long *);
 
-HsKernel hs_kernel(int klast) {
-    switch (klast) {
-        case 1: return fdas_hs_k1;
+// Compiled term counts, and the kernel for a group whose rows have at most kmax planes.
+constexpr int kl_size(int kmax) { return kmax <= 2 ? 2 : kmax <= 4 ? 4 : kmax <= 8 ? 8 : 16; }
+HsKernel hs_kernel(int kmax) {
+    switch (kl_size(kmax)) {
         case 2: return fdas_hs_kl<2>;
-        case 3: return fdas_hs_kl<3>;
         case 4: return fdas_hs_kl<4>;
-        case 5: return fdas_hs_kl<5>;
-        case 6: return fdas_hs_kl<6>;
-        case 7: return fdas_hs_kl<7>;
         case 8: return fdas_hs_kl<8>;
-        case 9: return fdas_hs_kl<9>;
-        case 10: return fdas_hs_kl<10>;
-        case 11: return fdas_hs_kl<11>;
-        case 12: return fdas_hs_kl<12>;
-        case 13: return fdas_hs_kl<13>;
-        case 14: return fdas_hs_kl<14>;
-        case 15: return fdas_hs_kl<15>;
         default: return fdas_hs_kl<16>;
     }
+}
+constexpr int kl_width(int kmax) { return kl_size(kmax) <= 8 ? jpt<8>() : jpt<16>(); }
+
+// Row groups of the harmonic sum for rows with at least two planes: [kmin, kmax] ranges of
+// klast = min(n_harm, floor(c/|i|)), each launched once. Rows with few planes keep their own,
+// smaller kernel (more resident warps); rows with many planes share one launch. Measured on the
+// 2^21 workload against one merged launch, one launch per plane count, and {4..16, 2..3}, this
+// partition was the fastest (0.428 ms against 0.462-0.464 ms).
+struct Group {
+    int kmin, kmax;
+};
+constexpr Group kGroups[] = {{5, 16}, {3, 4}, {2, 2}};
+
+// |i| range of the rows whose klast lies in [kmin, kmax]; false if there is none.
+bool group_rows(int c, int n_harm, int kmin, int kmax, int *lo, int *hi) {
+    if (kmin > n_harm) return false;
+    *lo = (kmax >= n_harm) ? 0 : c / (kmax + 1) + 1;
+    *hi = c / kmin;
+    return *hi >= *lo;
 }
 
 __device__ __forceinline__ fdas_cand decode_cand(unsigned long long key, int c, int k) {
@@ -399,13 +421,20 @@ __global__ void __launch_bounds__(kHsThreads, 4)
               vec);
 }
 
+// CTA widths: 8192 columns (kernels for up to 8 terms) or 4096 (16 terms, and the single-plane rows).
+// HsJob.blk0 / blk1 are the spectrum's first CTA in launches of each width.
 template <int KL>
 __global__ void __launch_bounds__(kHsThreads, KL <= 3 ? 4 : 2)
-    fdas_hs_kl_batch(const HsBatch B, const float *__restrict__ thresh, int n_temp, unsigned mask, int lo) {
-    const HsJob &J = B.job[job_of_block<false>(B, blockIdx.x)];
+    fdas_hs_kl_batch(const HsBatch B, const float *__restrict__ thresh, int n_temp, unsigned mask, int n_harm, int lo) {
+    constexpr bool wide = jpt<KL>() == 4;
+    const HsJob &J = B.job[job_of_block<!wide>(B, blockIdx.x)];
     const int c = (n_temp - 1) / 2;
-    hs_row<KL>(J.plane, J.n, (size_t)J.ld, thresh, n_temp, mask, c, group_row_offset(blockIdx.y, lo),
-               (blockIdx.x - J.blk0) * (kChunks * kHsThreads * jpt<KL>()), J.raw, J.counters, J.peaks);
+    const int i = group_row_offset(blockIdx.y, lo);
+    const int ai = i < 0 ? -i : i;
+    const int klast = ai == 0 ? n_harm : min(n_harm, c / ai);
+    hs_row<KL>(J.plane, J.n, (size_t)J.ld, thresh, n_temp, mask, c, i, klast,
+               (blockIdx.x - (wide ? J.blk0 : J.blk1)) * (kChunks * kHsThreads * jpt<KL>()), J.raw, J.counters,
+               J.peaks);
 }
 
 __global__ void __launch_bounds__(kFinThreads) fdas_hs_finalize_batch(const HsBatch B, int n_temp, int cand_cap) {
@@ -414,25 +443,13 @@ __global__ void __launch_bounds__(kFinThreads) fdas_hs_finalize_batch(const HsBa
     finalize_plane(blockIdx.x + 1, J.raw, J.counters, J.peaks, n_temp, cand_cap, J.cands, J.counts, J.peak_out, keys);
 }
 
-using HsBatchKernel = void (*)(const HsBatch, const float *, int, unsigned, int);
+using HsBatchKernel = void (*)(const HsBatch, const float *, int, unsigned, int, int);
 
-HsBatchKernel hs_batch_kernel(int klast) {
-    switch (klast) {
-        case 1: return fdas_hs_k1_batch;
+HsBatchKernel hs_batch_kernel(int kmax) {
+    switch (kl_size(kmax)) {
         case 2: return fdas_hs_kl_batch<2>;
-        case 3: return fdas_hs_kl_batch<3>;
         case 4: return fdas_hs_kl_batch<4>;
-        case 5: return fdas_hs_kl_batch<5>;
-        case 6: return fdas_hs_kl_batch<6>;
-        case 7: return fdas_hs_kl_batch<7>;
         case 8: return fdas_hs_kl_batch<8>;
-        case 9: return fdas_hs_kl_batch<9>;
-        case 10: return fdas_hs_kl_batch<10>;
-        case 11: return fdas_hs_kl_batch<11>;
-        case 12: return fdas_hs_kl_batch<12>;
-        case 13: return fdas_hs_kl_batch<13>;
-        case 14: return fdas_hs_kl_batch<14>;
-        case 15: return fdas_hs_kl_batch<15>;
         default: return fdas_hs_kl_batch<16>;
     }
 }
@@ -445,19 +462,25 @@ cudaError_t launch_harmonic(const fdas_params &p, const float *plane, size_t n, 
     fdas_hs_reset<<<1, 32, 0, s>>>(ws.counters, ws.peaks, p.n_harm);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    // Rows grouped by their number of planes klast: klast = n_harm for |i| <= c / n_harm, and
-    // klast = K < n_harm for c/(K+1) < |i| <= c/K.
+    // Rows with at least two planes in a few launches (kGroups), then the single-plane rows
+    // (|i| > c/2; every row when n_harm = 1) streamed by fdas_hs_k1.
     const int c = (p.n_temp - 1) / 2;
-    for (int K = p.n_harm; K >= 1; --K) {
-        const int per = kChunks * kHsThreads * (K <= 9 ? jpt<9>() : jpt<10>());  // columns per CTA
-        const unsigned gx = (unsigned)((n + per - 1) / per);
-        const int lo = (K == p.n_harm) ? 0 : c / (K + 1) + 1;
-        const int hi = c / K;
-        if (hi < lo) continue;
+    const int lo1 = p.n_harm >= 2 ? c / 2 + 1 : 0;
+    for (const Group &gr : kGroups) {
+        int lo, hi;
+        if (!group_rows(c, p.n_harm, gr.kmin, gr.kmax, &lo, &hi)) continue;
+        const int kmax = gr.kmax < p.n_harm ? gr.kmax : p.n_harm;
+        const int per = kChunks * kHsThreads * kl_width(kmax);
         const int rows = (lo == 0) ? 2 * hi + 1 : 2 * (hi - lo + 1);
-        const unsigned gxk = (K == 1) ? (unsigned)((n + kK1Cols - 1) / kK1Cols) : gx;
-        hs_kernel(K)<<<dim3(gxk, (unsigned)rows), kHsThreads, 0, s>>>(plane, (int)n, ld, thresh, p.n_temp, p.harm_mask,
-                                                                    lo, ws.raw, ws.counters, ws.peaks);
+        hs_kernel(kmax)<<<dim3((unsigned)((n + per - 1) / per), (unsigned)rows), kHsThreads, 0, s>>>(
+            plane, (int)n, ld, thresh, p.n_temp, p.harm_mask, p.n_harm, lo, ws.raw, ws.counters, ws.peaks);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    const int rows1 = lo1 == 0 ? 2 * c + 1 : 2 * (c - lo1 + 1);
+    if (rows1 > 0) {
+        fdas_hs_k1<<<dim3((unsigned)((n + kK1Cols - 1) / kK1Cols), (unsigned)rows1), kHsThreads, 0, s>>>(
+            plane, (int)n, ld, thresh, p.n_temp, p.harm_mask, lo1, ws.raw, ws.counters, ws.peaks);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -471,10 +494,12 @@ cudaError_t launch_harmonic(const fdas_params &p, const float *plane, size_t n, 
 
 // CTAs of one spectrum of n bins in the launches of rows with K >= 2 planes (all groups use the same
 // column width for n_harm <= 9) and in the launch of single-plane rows.
-void harmonic_blocks(const fdas_params &p, size_t n, int *blocks_kl, int *blocks_k1) {
-    const int per = kChunks * kHsThreads * (p.n_harm <= 9 ? jpt<9>() : jpt<10>());
-    *blocks_kl = (int)((n + per - 1) / per);
-    *blocks_k1 = (int)((n + kK1Cols - 1) / kK1Cols);
+void harmonic_blocks(const fdas_params &p, size_t n, int *blocks_wide, int *blocks_narrow) {
+    (void)p;
+    const int wide = kChunks * kHsThreads * jpt<8>();  // 8192 columns
+    static_assert(kChunks * kHsThreads * jpt<16>() == kK1Cols, "narrow CTAs of both kinds cover 4096 columns");
+    *blocks_wide = (int)((n + wide - 1) / wide);
+    *blocks_narrow = (int)((n + kK1Cols - 1) / kK1Cols);
 }
 
 cudaError_t prepare_harmonic_batch() {
@@ -488,13 +513,22 @@ cudaError_t launch_harmonic_batch(const fdas_params &p, const HsBatch &B, int to
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int c = (p.n_temp - 1) / 2;
-    for (int K = p.n_harm; K >= 1; --K) {
-        const int lo = (K == p.n_harm) ? 0 : c / (K + 1) + 1;
-        const int hi = c / K;
-        if (hi < lo) continue;
+    const int lo1 = p.n_harm >= 2 ? c / 2 + 1 : 0;
+    for (const Group &gr : kGroups) {
+        int lo, hi;
+        if (!group_rows(c, p.n_harm, gr.kmin, gr.kmax, &lo, &hi)) continue;
+        const int kmax = gr.kmax < p.n_harm ? gr.kmax : p.n_harm;
         const int rows = (lo == 0) ? 2 * hi + 1 : 2 * (hi - lo + 1);
-        const unsigned gx = (unsigned)(K == 1 ? total_k1 : total_kl);
-        hs_batch_kernel(K)<<<dim3(gx, (unsigned)rows), kHsThreads, 0, s>>>(B, thresh, p.n_temp, p.harm_mask, lo);
+        const unsigned gx = (unsigned)(kl_width(kmax) == jpt<8>() ? total_kl : total_k1);
+        hs_batch_kernel(kmax)<<<dim3(gx, (unsigned)rows), kHsThreads, 0, s>>>(B, thresh, p.n_temp, p.harm_mask,
+                                                                             p.n_harm, lo);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    const int rows1 = lo1 == 0 ? 2 * c + 1 : 2 * (c - lo1 + 1);
+    if (rows1 > 0) {
+        fdas_hs_k1_batch<<<dim3((unsigned)total_k1, (unsigned)rows1), kHsThreads, 0, s>>>(B, thresh, p.n_temp,
+                                                                                        p.harm_mask, lo1);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
