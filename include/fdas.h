@@ -102,6 +102,16 @@ fdas_status fdas_check_params(const fdas_params *p);
 /* Human-readable name of a status code. The string is static. */
 const char *fdas_status_string(fdas_status s);
 
+/* Device-side status of the current device: bit FDAS_DEV_WAIT_TIMEOUT is set when a kernel gave up
+ * on a bounded wait (the convolution waits on an mbarrier for each template's bulk copy, for about
+ * one second at most). Such a kernel still ends, but its outputs are not valid. The paper has no
+ * counterpart: its kernels run on an FPGA without such waits.
+ *   *flags receives the bits (OR over every launch since the last clear); clear != 0 zeroes them.
+ *   The read is synchronous with respect to the device (it waits for earlier work on the legacy
+ *   default stream). Returns FDAS_ERR_INVALID_ARG for a null flags, FDAS_ERR_CUDA if the read fails. */
+#define FDAS_DEV_WAIT_TIMEOUT 1u
+fdas_status fdas_device_status(uint32_t *flags, int clear);
+
 /* Size of the template bank written by fdas_make_templates: (n_temp + 1) * fft_len * 8 bytes.
  * Returns 0 for invalid parameters. */
 size_t fdas_templates_bytes(const fdas_params *p);

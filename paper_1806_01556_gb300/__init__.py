@@ -24,6 +24,7 @@ __all__ = [
     "CAND_DTYPE",
     "lib",
     "fdas_check_params",
+    "fdas_device_status",
     "fdas_templates_bytes",
     "fdas_plane_bytes",
     "fdas_workspace_bytes",
@@ -101,6 +102,13 @@ def _check(status: int, what: str) -> None:
 
 def fdas_check_params(p: Params) -> int:
     return lib().fdas_check_params(C.byref(p.c()))
+
+
+def fdas_device_status(clear: bool = False) -> int:
+    """Device status bits of the current device (FDAS_DEV_WAIT_TIMEOUT: a bounded wait gave up)."""
+    flags = C.c_uint32(0)
+    _check(lib().fdas_device_status(C.byref(flags), int(clear)), "fdas_device_status")
+    return flags.value
 
 
 def fdas_templates_bytes(p: Params) -> int:

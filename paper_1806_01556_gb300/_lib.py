@@ -16,6 +16,7 @@ FDAS_ERR_INVALID_ARG = -1
 FDAS_ERR_UNSUPPORTED = -2
 FDAS_ERR_WORKSPACE = -3
 FDAS_ERR_CUDA = -4
+FDAS_DEV_WAIT_TIMEOUT = 1
 
 FDAS_FP32, FDAS_BF16X3, FDAS_FP16S = 0, 1, 2
 FDAS_MAX_N = 1 << 24
@@ -83,6 +84,7 @@ SIGNATURES = {
     "fdas_default_params": (None, [P]),
     "fdas_check_params": (C.c_int, [P]),
     "fdas_status_string": (C.c_char_p, [C.c_int]),
+    "fdas_device_status": (C.c_int, [C.POINTER(C.c_uint32), C.c_int]),
     "fdas_templates_bytes": (SZ, [P]),
     "fdas_plane_bytes": (SZ, [P, SZ, SZ]),
     "fdas_workspace_bytes": (SZ, [P, SZ]),

@@ -87,6 +87,14 @@ const char *fdas_status_string(fdas_status s) {
     }
 }
 
+fdas_status fdas_device_status(uint32_t *flags, int clear) {
+    if (!flags) return FDAS_ERR_INVALID_ARG;
+    unsigned v = 0u;
+    if (fdas::device_status(&v, clear != 0) != cudaSuccess) return FDAS_ERR_CUDA;
+    *flags = v;
+    return FDAS_OK;
+}
+
 size_t fdas_templates_bytes(const fdas_params *p) {
     if (fdas_check_params(p) == FDAS_ERR_INVALID_ARG) return 0;
     return (size_t)(p->n_temp + 1) * (size_t)p->fft_len * 8u;

@@ -12,10 +12,11 @@
 // 16 x 16 x 8, with two shared-memory exchanges in a padded layout that is conflict-free for
 // 64-bit accesses. After the forward FFT, thread tid holds frequency m = tid + 128 q in register
 // q. This is exactly the input layout of the inverse FFT's first pass, so the product with the
-// template needs no exchange. The template values are read from global memory (the 1.4 MB bank
-// stays in L2) through a cp.async double buffer in shared memory, so the next template is in flight
+// template needs no exchange. Each template (16 KB, from the 1.4 MB bank that stays in L2) is
+// brought into a shared-memory double buffer by one TMA bulk copy, so the next template is in flight
 // while the current one is transformed. After the inverse FFT, thread tid holds time index
-// n = tid + 128 q, so the power stores of a warp are 32 consecutive columns.
+// n = tid + 128 q, so the power stores of a warp are 32 consecutive columns, issued as predicated
+// stores from one base pointer per template.
 #include <utility>
 
 #include "fdas_internal.cuh"
@@ -42,15 +43,40 @@ __device__ __forceinline__ float2 twiddle(float2 v, float2 w) {  // w = exp(-2 p
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 
-// Asynchronous 8-byte global -> shared copies (cp.async, completion tracked per thread in groups).
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all_but_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+// Status bits set on the device (read with fdas_device_status): a bounded wait gave up.
+__device__ unsigned int g_device_status;
 
-// Global store of one float under a predicate, without a branch.
-__device__ __forceinline__ void st_if(float *p, float v, unsigned pred) {
-    asm volatile(
-        "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q st.global.f32 [%0], %1;\n}\n" ::"l"(p), "f"(v), "r"(pred)
-        : "memory");
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// One-dimensional TMA bulk copy global -> shared, completing on an mbarrier (transaction count in bytes).
+__device__ __forceinline__ void mbar_init(unsigned long long *bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void tma_load(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+// Wait for phase `parity` of the mbarrier, for at most about 2^31 SM cycles (about one second). On
+// time-out the status word records it; the caller carries on, so the launch always ends.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
+    const long long start = clock64();
+    while (true) {
+        unsigned ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (clock64() - start > (1ll << 31)) {
+            atomicOr(&g_device_status, 1u);
+            return false;
+        }
+    }
 }
 
 // In-place 4-point DFT of (a, b, c, d) with sign exp(-+2 pi i / 4); outputs in natural order.
@@ -130,13 +156,14 @@ __device__ __forceinline__ void dft8(float2 (&v)[8]) {
 }
 
 // Passes 1 and 2 of the Stockham FFT: registers (A[tid + 128 r]) -> pass 1 -> buf0 -> pass 2 -> buf1.
-template <bool INV>
+template <bool INV, class AfterFirstBarrier>
 __device__ __forceinline__ void fft_passes_12(float2 (&v)[16], float2 *buf0, float2 *buf1, const float2 (&tw2)[16],
-                                              int tid) {
+                                              int tid, AfterFirstBarrier after_first_barrier) {
     dft16<INV>(v);
 #pragma unroll
     for (int r = 0; r < 16; ++r) buf0[pad(16 * tid + r)] = v[r];
     __syncthreads();
+    after_first_barrier();
 #pragma unroll
     for (int r = 0; r < 16; ++r) v[r] = buf0[pad(tid + 128 * r)];
 #pragma unroll
@@ -158,22 +185,8 @@ __device__ __forceinline__ void fft_pass_3(float2 (&u)[8], const float2 *buf1, c
     dft8<INV>(u);
 }
 
-// Each thread stages exactly the template values it multiplies (frequencies tid + 128 q), so the
-// double-buffered staging needs no barrier: cp.async.wait_group orders a thread's own copies.
-// sdst is the shared-memory address of the thread's first element; both strides are 1 KiB.
-template <int Q>
-__device__ __forceinline__ void cp_async8(unsigned sdst, const float2 *gsrc) {
-    asm volatile("cp.async.ca.shared.global [%0+%2], [%1+%2], 8;\n" ::"r"(sdst), "l"(gsrc), "n"(Q * 1024) : "memory");
-}
-template <int... Q>
-__device__ __forceinline__ void stage_template(unsigned sdst, const float2 *gsrc, std::integer_sequence<int, Q...>) {
-    (cp_async8<Q>(sdst, gsrc), ...);
-}
-__device__ __forceinline__ void stage_template(unsigned sdst, const float2 *gsrc) {
-    stage_template(sdst, gsrc, std::make_integer_sequence<int, 16>{});
-}
-
-constexpr size_t kSmemBytes = (2 * kPadded + 2 * kF) * sizeof(float2);  // two exchange + two template buffers
+// Two exchange buffers, two template buffers, and two mbarriers for the template copies.
+constexpr size_t kSmemBytes = (2 * kPadded + 2 * kF) * sizeof(float2) + 2 * sizeof(unsigned long long);
 
 // One work item: segment s of one spectrum with templates [t0, t1).
 struct Item {
@@ -229,11 +242,19 @@ struct BatchJobs {
 template <class Jobs>
 __global__ void __launch_bounds__(kThreads, 3)
     fdas_ols_fp32(Jobs jobs, const float2 *__restrict__ tmpl, int n_temp, int h, int keep) {
-    extern __shared__ float2 smem[];
+    extern __shared__ __align__(128) float2 smem[];
     float2 *buf0 = smem;
     float2 *buf1 = smem + kPadded;
     float2 *tbuf = smem + 2 * kPadded;  // [2][kF], template values of the current and next template
+    unsigned long long *tbar = reinterpret_cast<unsigned long long *>(smem + 2 * kPadded + 2 * kF);
     const int tid = threadIdx.x;
+    if (tid == 0) {
+        mbar_init(&tbar[0]);
+        mbar_init(&tbar[1]);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    unsigned phase = 0u;  // bit b: parity of the next completion of template buffer b
     const float2 *wtab = tmpl + (size_t)n_temp * kF;  // exp(-2 pi i k / F)
 
     // Stockham twiddles of this thread, fixed for the whole kernel.
@@ -276,10 +297,9 @@ __global__ void __launch_bounds__(kThreads, 3)
                 for (int r = 0; r < 8; ++r)
                     if (col0 + tid + 128 * hh + 256 * r >= n) smask &= ~(1u << (8 * hh + r));
         }
-        const unsigned tb0 = (unsigned)__cvta_generic_to_shared(tbuf + tid);
-        const unsigned tb1 = tb0 + kF * (unsigned)sizeof(float2);
-        stage_template(tb0, tmpl + (size_t)t0 * kF + tid);  // lands while the forward FFT runs
-        cp_async_commit();
+        // Template t0 lands in buffer 0 while the forward FFT runs. Every earlier read of buffer 0
+        // happened before a barrier that thread 0 has passed.
+        if (tid == 0) tma_load(tbuf, tmpl + (size_t)t0 * kF, kF * sizeof(float2), &tbar[0]);
 
         // Forward FFT of the segment: W[q] = DFT(w_s)[tid + 128 q] / F.
         float2 v[16];
@@ -288,7 +308,7 @@ __global__ void __launch_bounds__(kThreads, 3)
             const int idx = origin + tid + 128 * r;
             v[r] = (idx >= 0 && idx < n) ? __ldg(&spec[idx]) : make_float2(0.f, 0.f);
         }
-        fft_passes_12<false>(v, buf0, buf1, tw2, tid);
+        fft_passes_12<false>(v, buf0, buf1, tw2, tid, [] {});
         float2 W[16];
         {
             float2 u[8];
@@ -302,23 +322,31 @@ __global__ void __launch_bounds__(kThreads, 3)
 
         for (int t = t0; t < t1; ++t) {
             const int slot = (t - t0) & 1;
-            // Stage the next template (the last one again on the final iteration: no branch).
-            stage_template(slot ? tb0 : tb1, tmpl + (size_t)min(t + 1, t1 - 1) * kF + tid);
-            cp_async_commit();
-            cp_async_wait_all_but_one();  // this thread's copies of template t have landed
+            mbar_wait(&tbar[slot], (phase >> slot) & 1u);  // template t is in buffer slot
+            phase ^= 1u << slot;
             const float2 *T = tbuf + slot * kF + tid;
 #pragma unroll
             for (int q = 0; q < 16; ++q) v[q] = cmul(W[q], T[128 * q]);
-            fft_passes_12<true>(v, buf0, buf1, tw2, tid);
-            float *row = it.plane + (size_t)t * it.ld;
+            // After the first barrier of this FFT every thread has read buffer slot^1 for the last
+            // time (in the previous template), so thread 0 refills it with template t + 1.
+            fft_passes_12<true>(v, buf0, buf1, tw2, tid, [&] {
+                if (tid == 0 && t + 1 < t1)
+                    tma_load(tbuf + (slot ^ 1) * kF, tmpl + (size_t)(t + 1) * kF, kF * sizeof(float2),
+                             &tbar[slot ^ 1]);
+            });
+            // Column col0 + b + 256 r of row t, for b = tid + 128 hh: one base pointer per half, then
+            // constant offsets; a plain predicated store per output.
+            float *const dst = it.plane + (size_t)t * it.ld + col0 + tid;
 #pragma unroll
             for (int hh = 0; hh < 2; ++hh) {
                 float2 u[8];
-                const int b = tid + 128 * hh;
-                fft_pass_3<true>(u, buf1, hh ? tw3b : tw3a, b);
+                fft_pass_3<true>(u, buf1, hh ? tw3b : tw3a, tid + 128 * hh);
+                const unsigned m8 = smask >> (8 * hh);
 #pragma unroll
-                for (int r = 0; r < 8; ++r)
-                    st_if(row + col0 + b + 256 * r, fmaf(u[r].x, u[r].x, u[r].y * u[r].y), (smask >> (8 * hh + r)) & 1u);
+                for (int r = 0; r < 8; ++r) {
+                    const float pw = fmaf(u[r].x, u[r].x, u[r].y * u[r].y);
+                    if ((m8 >> r) & 1u) dst[128 * hh + 256 * r] = pw;
+                }
             }
         }
     }
@@ -360,6 +388,15 @@ cudaError_t launch_convolve_fp32(const Geometry &g, const float2 *spec, size_t n
     if (e != cudaSuccess) return e;
     fdas_ols_fp32<<<grid, kThreads, kSmemBytes, s>>>(jobs, tmpl, g.n_temp, g.h, g.keep);
     return cudaGetLastError();
+}
+
+cudaError_t device_status(unsigned *flags, bool clear) {
+    cudaError_t e = cudaMemcpyFromSymbol(flags, g_device_status, sizeof(unsigned));
+    if (e == cudaSuccess && clear) {
+        const unsigned zero = 0u;
+        e = cudaMemcpyToSymbol(g_device_status, &zero, sizeof(unsigned));
+    }
+    return e;
 }
 
 cudaError_t prepare_convolve_batch() {

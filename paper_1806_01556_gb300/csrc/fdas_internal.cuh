@@ -88,6 +88,8 @@ struct HsBatch {
 cudaError_t launch_templates(const fdas_params &p, void *d_tmpl, cudaStream_t s);
 cudaError_t launch_convolve_fp32(const Geometry &g, const float2 *spec, size_t n, const float2 *tmpl,
                                  float *plane, size_t ld, int ctas_per_sm, int templates_per_item, cudaStream_t s);
+// Status bits set by kernels on the device (bit 0: a bounded wait timed out); optionally cleared.
+cudaError_t device_status(unsigned *flags, bool clear);
 // Batched convolution: one persistent launch over every segment of every spectrum.
 cudaError_t prepare_convolve_batch();
 int convolve_items(const Geometry &g, size_t n, int templates_per_item);

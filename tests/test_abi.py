@@ -122,6 +122,7 @@ def test_bad_pointers_are_rejected_before_any_launch(fd):
                                 null, fake, ws, null) == -1
     assert lib.fdas_default_thresholds(C.byref(p), 6.0, 2, fake) == -1
     assert lib.fdas_status_string(-3) == b"workspace too small"
+    assert lib.fdas_device_status(None, 0) == -1
 
 
 class _NullStream:

@@ -289,3 +289,14 @@ def test_search_candidates_match_oracle_within_tolerance(fd, small_case):
         for q in set(r) - set(g):
             assert r[q] <= ta[k - 1, 0] * (1 + tol)
     assert (int(cands[0][0]["i"]), int(cands[0][0]["j"])) == (20, 12000)
+
+
+def test_no_bounded_wait_gave_up(fd, small_case):
+    """The convolution's bounded waits on its template copies all completed in every launch so far."""
+    wl, _ = small_case
+    p = fd.Params()
+    s = fd.Searcher(p, wl.n)
+    s.search(torch.from_numpy(wl.spectrum).cuda(), wl.n)
+    torch.cuda.synchronize()
+    assert fd.fdas_device_status(clear=True) == 0
+    assert fd.fdas_device_status() == 0
