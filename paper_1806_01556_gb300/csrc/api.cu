@@ -72,7 +72,7 @@ fdas_status fdas_check_params(const fdas_params *p) {
     if (p->cand_cap < 1 || p->cand_cap > FDAS_MAX_CAND_CAP) return FDAS_ERR_INVALID_ARG;
     if (p->precision != FDAS_FP32 && p->precision != FDAS_BF16X3 && p->precision != FDAS_FP16S)
         return FDAS_ERR_INVALID_ARG;
-    if (p->fft_len != 2048 || p->precision != FDAS_FP32) return FDAS_ERR_UNSUPPORTED;
+    if (p->fft_len != 2048) return FDAS_ERR_UNSUPPORTED;
     return FDAS_OK;
 }
 
@@ -141,8 +141,8 @@ fdas_status fdas_convolve_cfg(const fdas_params *p, const void *d_spec, size_t n
     const int tpi = cfg ? cfg->templates_per_item : 0;
     if (ctas < 0 || ctas > 64 || tpi < 0) return FDAS_ERR_INVALID_ARG;
     const Geometry g = fdas::geometry(*p);
-    return cuda_status(fdas::launch_convolve_fp32(g, static_cast<const float2 *>(d_spec), n,
-                                                  static_cast<const float2 *>(d_tmpl), d_plane, ld, ctas, tpi, stream));
+    return cuda_status(fdas::launch_convolve(g, static_cast<const float2 *>(d_spec), n,
+                                             static_cast<const float2 *>(d_tmpl), d_plane, ld, ctas, tpi, stream));
 }
 
 fdas_status fdas_convolve(const fdas_params *p, const void *d_spec, size_t n, const void *d_tmpl, float *d_plane,

@@ -99,7 +99,8 @@ cudaError_t prepare() {
 cudaError_t launch_batch(const fdas_params &p, const Tables &t, const void *d_tmpl, const float *d_thresh, int sms,
                          const fdas_launch_config &cfg, cudaStream_t s, bool conv_only = false) {
     const fdas::Geometry g = fdas::geometry(p);
-    const int ctas = cfg.ctas_per_sm > 0 ? cfg.ctas_per_sm : 3;  // 3 CTAs fit per SM
+    const int max_ctas = fdas::convolve_ctas_per_sm(g);  // resident CTAs per SM
+    const int ctas = cfg.ctas_per_sm > 0 && cfg.ctas_per_sm < max_ctas ? cfg.ctas_per_sm : max_ctas;
     const int grid = t.conv.total_items < ctas * sms ? t.conv.total_items : ctas * sms;
     cudaError_t e = fdas::launch_convolve_batch(g, t.conv, static_cast<const float2 *>(d_tmpl), grid,
                                                 cfg.templates_per_item, s);

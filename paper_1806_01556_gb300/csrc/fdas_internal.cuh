@@ -17,6 +17,7 @@ struct Geometry {
     int h;        // half width, (n_tap-1)/2
     int fft_len;  // overlap-save segment length F
     int keep;     // valid outputs per segment, L = F - n_tap + 1
+    int precision;  // FDAS_FP32, FDAS_BF16X3 or FDAS_FP16S
 };
 
 inline Geometry geometry(const fdas_params &p) {
@@ -27,6 +28,7 @@ inline Geometry geometry(const fdas_params &p) {
     g.h = (p.n_tap - 1) / 2;
     g.fft_len = p.fft_len;
     g.keep = p.fft_len - p.n_tap + 1;
+    g.precision = p.precision;
     return g;
 }
 
@@ -86,8 +88,22 @@ struct HsBatch {
 
 // Kernel launchers (each returns cudaGetLastError() of its launch).
 cudaError_t launch_templates(const fdas_params &p, void *d_tmpl, cudaStream_t s);
+// Convolution launch for g.precision: the FP32 kernel or the tensor-core kernel.
+cudaError_t launch_convolve(const Geometry &g, const float2 *spec, size_t n, const float2 *tmpl, float *plane,
+                            size_t ld, int ctas_per_sm, int templates_per_item, cudaStream_t s);
 cudaError_t launch_convolve_fp32(const Geometry &g, const float2 *spec, size_t n, const float2 *tmpl,
                                  float *plane, size_t ld, int ctas_per_sm, int templates_per_item, cudaStream_t s);
+// Tensor-core form: two CTAs per SM at most (Tensor Memory), default 44 templates per work item.
+constexpr int kTcMaxCtasPerSm = 2;
+constexpr int kTcDefaultTemplatesPerItem = 44;
+cudaError_t launch_convolve_tc(const Geometry &g, const float2 *spec, size_t n, const float2 *tmpl, float *plane,
+                               size_t ld, int ctas_per_sm, int templates_per_item, cudaStream_t s);
+cudaError_t prepare_convolve_batch_tc();
+cudaError_t launch_convolve_batch_tc(const Geometry &g, const ConvBatch &batch, const float2 *tmpl, int grid,
+                                     int templates_per_item, cudaStream_t s);
+cudaError_t device_status_tc(unsigned *flags, bool clear);
+// Resident CTAs per SM of the convolution kernel for g.precision.
+inline int convolve_ctas_per_sm(const Geometry &g) { return g.precision == FDAS_FP32 ? 3 : kTcMaxCtasPerSm; }
 // Status bits set by kernels on the device (bit 0: a bounded wait timed out); optionally cleared.
 cudaError_t device_status(unsigned *flags, bool clear);
 // Batched convolution: one persistent launch over every segment of every spectrum.

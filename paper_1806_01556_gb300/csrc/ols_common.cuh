@@ -1,0 +1,225 @@
+// Pieces shared by the overlap-save convolution kernels (FP32 and tensor-core forms): the
+// 2048-point FFT in registers (radix 16 x 16 x 8 Stockham passes through a padded shared-memory
+// buffer), the TMA bulk copy with its bounded mbarrier wait, and the work-item decomposition
+// (segment s of a spectrum with a range of templates). Everything here has internal linkage, so
+// each translation unit that includes it has its own copy, including its own status word.
+#pragma once
+#include "fdas_internal.cuh"
+
+namespace fdas {
+namespace {
+
+constexpr int kF = 2048;
+constexpr int kThreads = 128;
+constexpr int kPadded = kF + kF / 16;  // one pad element after every 16
+
+__device__ __forceinline__ int pad(int e) { return e + (e >> 4); }
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cmul_conj(float2 a, float2 b) {  // a * conj(b)
+    return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+template <bool INV>
+__device__ __forceinline__ float2 twiddle(float2 v, float2 w) {  // w = exp(-2 pi i x); INV uses conj(w)
+    return INV ? cmul_conj(v, w) : cmul(v, w);
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+
+// Status bits set on the device (read with fdas_device_status): a bounded wait gave up.
+__device__ unsigned int g_device_status;
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// One-dimensional TMA bulk copy global -> shared, completing on an mbarrier (transaction count in bytes).
+__device__ __forceinline__ void mbar_init(unsigned long long *bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void tma_load(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+// Wait for phase `parity` of the mbarrier, for at most about 2^31 SM cycles (about one second). On
+// time-out the status word records it; the caller carries on, so the launch always ends.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
+    const long long start = clock64();
+    while (true) {
+        unsigned ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (clock64() - start > (1ll << 31)) {
+            atomicOr(&g_device_status, 1u);
+            return false;
+        }
+    }
+}
+
+// In-place 4-point DFT of (a, b, c, d) with sign exp(-+2 pi i / 4); outputs in natural order.
+template <bool INV>
+__device__ __forceinline__ void dft4(float2 &a, float2 &b, float2 &c, float2 &d) {
+    const float2 s0 = cadd(a, c), s1 = csub(a, c), s2 = cadd(b, d), s3 = csub(b, d);
+    a = cadd(s0, s2);
+    c = csub(s0, s2);
+    if (!INV) {
+        b = make_float2(s1.x + s3.y, s1.y - s3.x);  // s1 - i s3
+        d = make_float2(s1.x - s3.y, s1.y + s3.x);  // s1 + i s3
+    } else {
+        b = make_float2(s1.x - s3.y, s1.y + s3.x);
+        d = make_float2(s1.x + s3.y, s1.y - s3.x);
+    }
+}
+
+// Multiply by exp(-+2 pi i m / 16) for the constant m (0 < m < 16).
+template <bool INV, int M>
+__device__ __forceinline__ float2 w16(float2 v) {
+    constexpr float c1 = 0.92387953251128674f, s1 = 0.38268343236508977f, r = 0.70710678118654752f;
+    constexpr int m = M & 15;
+    constexpr float wr = m == 0 ? 1.f : m == 1 ? c1 : m == 2 ? r : m == 3 ? s1 : m == 4 ? 0.f : m == 5 ? -s1
+                       : m == 6 ? -r : m == 7 ? -c1 : m == 8 ? -1.f : m == 9 ? -c1 : m == 10 ? -r : m == 11 ? -s1
+                       : m == 12 ? 0.f : m == 13 ? s1 : m == 14 ? r : c1;
+    constexpr float wi0 = m == 0 ? 0.f : m == 1 ? -s1 : m == 2 ? -r : m == 3 ? -c1 : m == 4 ? -1.f : m == 5 ? -c1
+                        : m == 6 ? -r : m == 7 ? -s1 : m == 8 ? 0.f : m == 9 ? s1 : m == 10 ? r : m == 11 ? c1
+                        : m == 12 ? 1.f : m == 13 ? c1 : m == 14 ? r : s1;
+    constexpr float wi = INV ? -wi0 : wi0;
+    if (m == 4) return INV ? make_float2(-v.y, v.x) : make_float2(v.y, -v.x);
+    return make_float2(fmaf(v.x, wr, -v.y * wi), fmaf(v.x, wi, v.y * wr));
+}
+
+// 16-point DFT in registers, natural order in and out: radix 4 x 4 with internal twiddles.
+template <bool INV>
+__device__ __forceinline__ void dft16(float2 (&v)[16]) {
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) dft4<INV>(v[n2], v[4 + n2], v[8 + n2], v[12 + n2]);
+    // v[4 k1 + n2] *= W16^(n2 k1)
+    v[5] = w16<INV, 1>(v[5]);
+    v[6] = w16<INV, 2>(v[6]);
+    v[7] = w16<INV, 3>(v[7]);
+    v[9] = w16<INV, 2>(v[9]);
+    v[10] = w16<INV, 4>(v[10]);
+    v[11] = w16<INV, 6>(v[11]);
+    v[13] = w16<INV, 3>(v[13]);
+    v[14] = w16<INV, 6>(v[14]);
+    v[15] = w16<INV, 9>(v[15]);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) dft4<INV>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+    // v[4 k1 + k2] holds X[k1 + 4 k2]: transpose the 4 x 4 register block.
+    float2 t[16];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) t[k1 + 4 * k2] = v[4 * k1 + k2];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = t[i];
+}
+
+// 8-point DFT in registers, natural order in and out: radix 4 x 2.
+template <bool INV>
+__device__ __forceinline__ void dft8(float2 (&v)[8]) {
+    dft4<INV>(v[0], v[2], v[4], v[6]);
+    dft4<INV>(v[1], v[3], v[5], v[7]);
+    v[3] = w16<INV, 2>(v[3]);  // W8^1
+    v[5] = w16<INV, 4>(v[5]);  // W8^2
+    v[7] = w16<INV, 6>(v[7]);  // W8^3
+    float2 t[8];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+        t[k1] = cadd(v[2 * k1], v[2 * k1 + 1]);
+        t[k1 + 4] = csub(v[2 * k1], v[2 * k1 + 1]);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = t[i];
+}
+
+// Passes 1 and 2 of the Stockham FFT: registers (A[tid + 128 r]) -> pass 1 -> buf0 -> pass 2 -> buf1.
+template <bool INV, class AfterFirstBarrier>
+__device__ __forceinline__ void fft_passes_12(float2 (&v)[16], float2 *buf0, float2 *buf1, const float2 (&tw2)[16],
+                                              int tid, AfterFirstBarrier after_first_barrier) {
+    dft16<INV>(v);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) buf0[pad(16 * tid + r)] = v[r];
+    __syncthreads();
+    after_first_barrier();
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = buf0[pad(tid + 128 * r)];
+#pragma unroll
+    for (int r = 1; r < 16; ++r) v[r] = twiddle<INV>(v[r], tw2[r]);
+    dft16<INV>(v);
+    const int base = (tid >> 4) * 256 + (tid & 15);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) buf1[pad(base + 16 * r)] = v[r];
+    __syncthreads();
+}
+
+// Pass 3 for butterfly b = tid + 128 hh: reads buf1[b + 256 r], returns index b + 256 r in u[r].
+template <bool INV>
+__device__ __forceinline__ void fft_pass_3(float2 (&u)[8], const float2 *buf1, const float2 (&tw3)[8], int b) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) u[r] = buf1[pad(b + 256 * r)];
+#pragma unroll
+    for (int r = 1; r < 8; ++r) u[r] = twiddle<INV>(u[r], tw3[r]);
+    dft8<INV>(u);
+}
+
+// One work item: segment s of one spectrum with templates [t0, t1).
+struct Item {
+    const float2 *spec;
+    float *plane;
+    size_t ld;
+    int n;
+    int s;
+    int t0;
+    int t1;
+};
+
+// Work items of a single spectrum: item = s * n_tchunk + chunk.
+struct SingleJobs {
+    const float2 *spec;
+    float *plane;
+    size_t ld;
+    int n;
+    int n_seg;
+    int t_chunk;
+    int n_tchunk;
+    int n_temp;
+    __device__ int total() const { return n_seg * n_tchunk; }
+    __device__ Item get(int item) const {
+        const int s = item / n_tchunk;
+        const int t0 = (item - s * n_tchunk) * t_chunk;
+        return Item{spec, plane, ld, n, s, t0, min(t0 + t_chunk, n_temp)};
+    }
+};
+
+// Work items of a batch (a kernel parameter): the items of spectrum b are
+// [job[b].item0, job[b].item0 + n_seg_b * n_tchunk).
+struct BatchJobs {
+    ConvBatch batch;
+    int t_chunk;
+    int n_tchunk;
+    int n_temp;
+    __device__ int total() const { return batch.total_items; }
+    __device__ Item get(int item) const {
+        int lo = 0, hi = batch.count - 1;  // last job with item0 <= item
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (batch.job[mid].item0 <= item) lo = mid; else hi = mid - 1;
+        }
+        const ConvJob &J = batch.job[lo];
+        const int local = item - J.item0;
+        const int s = local / n_tchunk;
+        const int t0 = (local - s * n_tchunk) * t_chunk;
+        return Item{J.spec, J.plane, (size_t)J.ld, J.n, s, t0, min(t0 + t_chunk, n_temp)};
+    }
+};
+
+}  // namespace
+}  // namespace fdas

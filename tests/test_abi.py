@@ -78,7 +78,9 @@ def test_defaults_and_sizes(fd):
         (dict(cand_cap=5000), -1),
         (dict(precision=7), -1),
         (dict(fft_len=4096), -2),
-        (dict(precision=1), -2),
+        (dict(precision=1, fft_len=4096), -2),
+        (dict(precision=1), 0),
+        (dict(precision=2), 0),
         (dict(n_temp=9, z_min=-8, z_step=2), 0),
         (dict(n_harm=16, harm_mask=0xFFFF), 0),
     ],
