@@ -93,8 +93,8 @@ cudaError_t launch_convolve(const Geometry &g, const float2 *spec, size_t n, con
                             size_t ld, int ctas_per_sm, int templates_per_item, cudaStream_t s);
 cudaError_t launch_convolve_fp32(const Geometry &g, const float2 *spec, size_t n, const float2 *tmpl,
                                  float *plane, size_t ld, int ctas_per_sm, int templates_per_item, cudaStream_t s);
-// Tensor-core form: two CTAs per SM at most (Tensor Memory), default 44 templates per work item.
-constexpr int kTcMaxCtasPerSm = 2;
+// Tensor-core form: one CTA per SM (all of Tensor Memory), default 44 templates per work item.
+constexpr int kTcMaxCtasPerSm = 1;
 constexpr int kTcDefaultTemplatesPerItem = 44;
 cudaError_t launch_convolve_tc(const Geometry &g, const float2 *spec, size_t n, const float2 *tmpl, float *plane,
                                size_t ld, int ctas_per_sm, int templates_per_item, cudaStream_t s);

@@ -46,15 +46,17 @@ __device__ __forceinline__ void tma_load(void *dst, const void *src, unsigned by
                  : "memory");
 }
 // Wait for phase `parity` of the mbarrier, for at most about 2^31 SM cycles (about one second). On
-// time-out the status word records it; the caller carries on, so the launch always ends.
+// time-out the status word records it; the caller carries on, so the launch always ends. Each
+// try_wait may suspend the thread until the phase completes, for at most 1 ms (the hint, in ns),
+// so a waiting warp takes few issue slots from the others.
 __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
     const long long start = clock64();
     while (true) {
         unsigned ok;
         asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}\n"
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n}\n"
             : "=r"(ok)
-            : "r"(smem_u32(bar)), "r"(parity)
+            : "r"(smem_u32(bar)), "r"(parity), "r"(1000000u)
             : "memory");
         if (ok) return true;
         if (clock64() - start > (1ll << 31)) {
@@ -141,13 +143,14 @@ __device__ __forceinline__ void dft8(float2 (&v)[8]) {
 }
 
 // Passes 1 and 2 of the Stockham FFT: registers (A[tid + 128 r]) -> pass 1 -> buf0 -> pass 2 -> buf1.
-template <bool INV, class AfterFirstBarrier>
+// `sync` synchronises the 128 threads that run the FFT (the whole CTA by default).
+template <bool INV, class AfterFirstBarrier, class Sync>
 __device__ __forceinline__ void fft_passes_12(float2 (&v)[16], float2 *buf0, float2 *buf1, const float2 (&tw2)[16],
-                                              int tid, AfterFirstBarrier after_first_barrier) {
+                                              int tid, AfterFirstBarrier after_first_barrier, Sync sync) {
     dft16<INV>(v);
 #pragma unroll
     for (int r = 0; r < 16; ++r) buf0[pad(16 * tid + r)] = v[r];
-    __syncthreads();
+    sync();
     after_first_barrier();
 #pragma unroll
     for (int r = 0; r < 16; ++r) v[r] = buf0[pad(tid + 128 * r)];
@@ -157,7 +160,12 @@ __device__ __forceinline__ void fft_passes_12(float2 (&v)[16], float2 *buf0, flo
     const int base = (tid >> 4) * 256 + (tid & 15);
 #pragma unroll
     for (int r = 0; r < 16; ++r) buf1[pad(base + 16 * r)] = v[r];
-    __syncthreads();
+    sync();
+}
+template <bool INV, class AfterFirstBarrier>
+__device__ __forceinline__ void fft_passes_12(float2 (&v)[16], float2 *buf0, float2 *buf1, const float2 (&tw2)[16],
+                                              int tid, AfterFirstBarrier after_first_barrier) {
+    fft_passes_12<INV>(v, buf0, buf1, tw2, tid, after_first_barrier, [] { __syncthreads(); });
 }
 
 // Pass 3 for butterfly b = tid + 128 hh: reads buf1[b + 256 r], returns index b + 256 r in u[r].
