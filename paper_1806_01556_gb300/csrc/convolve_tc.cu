@@ -21,21 +21,21 @@
 // have unit energy); the 64-term sums D1 are FP32 and the twiddles carry a factor 2^-6 that the
 // power rescaling 2^(12 - 2k) undoes.
 //
-// One persistent CTA per SM, 9 warps with fixed roles, templates in pairs (pair p of the CTA uses
-// buffer slot p & 1 of each double buffer):
-//   prep  (warps 0-3)   forward FFT of each segment; U = W * T_t, split, stored as the GEMM's B
-//                       operand in shared memory (rows: 2 templates x 32 m1, K: 64 m2 x re/im);
-//                       templates arrive by TMA bulk copies into a ring of eight slots;
-//   MMA   (warp 4)      one thread issues 24 MMAs per pair (M = 128, N = 64, K = 128; A = the
+// One persistent CTA per SM runs three independent worker groups of 4 warps; each group owns a
+// stream of work items (a segment with a range of templates) and its own shared-memory operand
+// and TMEM accumulator, and is served by its own MMA-issue warp:
+//   prep  (group)       forward FFT of the segment (W kept in shared memory); per pair of templates
+//                       U = W * T_t (templates read from L2), split, stored as the GEMM's B operand
+//                       (rows: 2 templates x 32 m1, K: 64 m2 x re/im);
+//   MMA   (warp 12 + g) one thread issues 24 MMAs per pair (M = 128, N = 64, K = 128; A = the
 //                       real-form 64-point DFT matrix, both halves, resident in Tensor Memory);
-//   mid   (warps 5-8)   D1 from TMEM (each thread holds the real or the imaginary row of one n2; the
+//   mid   (group)       D1 from TMEM (each thread holds the real or the imaginary row of one n2; the
 //                       partner lane 16 away holds the other), the twiddle product, a 32-point DFT
 //                       in registers (radix 4 x 8), |u|^2 of the kept outputs, coalesced stores.
-// The roles hand buffers to each other through mbarriers (full/empty per slot), so the tensor
-// cores run one pair's GEMM while the CUDA cores prepare the next and finish the previous. Every
-// wait is bounded: a wait that gives up sets the device status word and an abort flag, after which
-// no role issues work or waits again; before freeing its TMEM the CTA waits once more, bounded,
-// for whatever it had issued.
+// While one group waits for its GEMM the other two keep the CUDA cores busy, and the tensor cores
+// take the three groups' GEMMs in turn. Every wait is bounded: a wait that gives up sets the device
+// status word and an abort flag, after which no role issues work or waits again; before freeing its
+// TMEM the CTA waits once more, bounded, for whatever it had issued.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -45,26 +45,26 @@
 namespace fdas {
 namespace {
 
-constexpr int kPrepWarps = 4, kMmaWarp = 4;  // mid: warps 5-8
-constexpr int kTcThreads = 9 * 32;
-constexpr uint32_t kTmemCols = 256;
-// Tensor Memory columns: the DFT matrix (hi, lo), then D1[2].
+constexpr int kGroups = 3;                            // worker groups of 4 warps
+constexpr int kMmaWarp0 = 4 * kGroups;                // MMA-issue warps 12, 13, 14
+constexpr int kTcThreads = (4 * kGroups + kGroups) * 32;
+constexpr uint32_t kTmemCols = 512;
+// Tensor Memory columns: the DFT matrix (hi, lo), then one D1 per group.
 constexpr uint32_t kColAhi = 0, kColAlo = 64, kColD1 = 128;
 
-// Shared memory (bytes).
+// Shared memory (bytes), per group: region X (the forward FFT's exchange buffers, then the GEMM's
+// B operand, hi and lo) and W; then the twiddle table, barriers and small state.
 constexpr int kB1Term = 64 * 128 * 2;                 // rows (t_local, m1) x K (m2, re/im), 16-bit
-constexpr int kB1Slot = 2 * kB1Term;                  // hi, lo
-constexpr int kOffB1 = 0;                             // two slots; the forward FFT's buffers alias them
-constexpr int kTSlots = 8;                            // template ring
-constexpr int kOffT = kOffB1 + 2 * kB1Slot;
+constexpr int kXBytes = 2 * kPadded * 8;
+constexpr int kGroupBytes = kXBytes + kF * 8;         // region X + W
 constexpr int kTwRow = 32 * 8 + 16;                   // 32 twiddles per n2 row, padded by 16 bytes
-constexpr int kOffTw = kOffT + kTSlots * kF * 8;
+constexpr int kOffTw = kGroups * kGroupBytes;
 constexpr int kOffBar = kOffTw + 64 * kTwRow;
-constexpr int kNumBars = kTSlots + 9;
+constexpr int kNumBars = 2 * kGroups + 1;
 constexpr int kOffMisc = kOffBar + kNumBars * 8;
-constexpr int kTcSmemBytes = kOffMisc + 96;
-static_assert(2 * kPadded * 8 <= 2 * kB1Slot, "the FFT buffers fit in the two operand slots");
-static_assert(kOffT % 128 == 0 && kOffTw % 16 == 0 && kOffBar % 8 == 0, "alignment");
+constexpr int kTcSmemBytes = kOffMisc + 16 + 16 * kGroups + 64 * kGroups;
+static_assert(2 * kB1Term <= kXBytes, "the operand fits in the FFT's region");
+static_assert(kGroupBytes % 1024 == 0 && kOffTw % 16 == 0 && kOffBar % 8 == 0, "alignment");
 static_assert(kTcSmemBytes <= 227 * 1024, "shared memory per CTA");
 
 // Byte offset of element (row, k) in a K-major operand without swizzle: 8 x 8 core matrices of
@@ -102,19 +102,6 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
 }
 __device__ __forceinline__ void mbar_init_n(unsigned long long *bar, unsigned count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-// Named barrier of the four prep warps.
-__device__ __forceinline__ void prep_sync() { asm volatile("bar.sync 1, 128;\n" ::: "memory"); }
-
-// One template (16 KB) into a ring slot, completing on the slot's mbarrier.
-__device__ __forceinline__ void load_template(float2 *dst, const float2 *src, unsigned long long *bar) {
-    const unsigned bytes = (unsigned)(kF * sizeof(float2));
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
 }
 
 // v * e^{2 pi i k / 32} for k known at compile time after unrolling.
@@ -155,34 +142,32 @@ __device__ __forceinline__ void idft32(float2 (&v)[32]) {
     for (int i = 0; i < 32; ++i) v[i] = u[i];
 }
 
-// Barrier indices.
-enum : int { kBarT = 0, kBarB1Full = kTSlots, kBarB1Empty = kTSlots + 2, kBarD1Full = kTSlots + 4,
-             kBarD1Empty = kTSlots + 6, kBarFin = kTSlots + 8 };
+// Barrier indices: per group g, B1 full (4 warp arrivals) and D1 full (MMA commit).
+__device__ __forceinline__ int bar_b1full(int g) { return 2 * g; }
+__device__ __forceinline__ int bar_d1full(int g) { return 2 * g + 1; }
+constexpr int kBarFin = 2 * kGroups;
+
+// Named barrier of group g's four warps (ids 1..kGroups).
+__device__ __forceinline__ void group_sync(int g) { asm volatile("bar.sync %0, 128;\n" ::"r"(g + 1) : "memory"); }
 
 template <bool HALF, class Jobs>
 __global__ void __launch_bounds__(kTcThreads, 1)
     fdas_ols_tc(Jobs jobs, const float2 *__restrict__ tmpl, int n_temp, int h, int keep) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char *const b1 = smem + kOffB1;
-    float2 *const tring = reinterpret_cast<float2 *>(smem + kOffT);
     unsigned char *const twt = smem + kOffTw;
     unsigned long long *const bars = reinterpret_cast<unsigned long long *>(smem + kOffBar);
     uint32_t *const tslot = reinterpret_cast<uint32_t *>(smem + kOffMisc);
     volatile int *const aborted = reinterpret_cast<volatile int *>(smem + kOffMisc + 4);
-    unsigned *const red = reinterpret_cast<unsigned *>(smem + kOffMisc + 16);      // [4]
-    float *const scale_ring = reinterpret_cast<float *>(smem + kOffMisc + 32);     // [16]
 
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     const float2 *wtab = tmpl + (size_t)n_temp * kF;  // exp(-2 pi i k / F)
     const int n_items = jobs.total();
+    const int n_virt = gridDim.x * kGroups;  // worker groups across the grid
 
     if (tid == 0) {
-        for (int i = 0; i < kTSlots; ++i) mbar_init_n(&bars[kBarT + i], 1);
-        for (int i = 0; i < 2; ++i) {
-            mbar_init_n(&bars[kBarB1Full + i], kPrepWarps);
-            mbar_init_n(&bars[kBarB1Empty + i], 1);
-            mbar_init_n(&bars[kBarD1Full + i], 1);
-            mbar_init_n(&bars[kBarD1Empty + i], 4);
+        for (int g = 0; g < kGroups; ++g) {
+            mbar_init_n(&bars[bar_b1full(g)], 4);
+            mbar_init_n(&bars[bar_d1full(g)], 1);
         }
         mbar_init_n(&bars[kBarFin], 1);
         *aborted = 0;
@@ -232,89 +217,99 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     __syncthreads();
     tc::fence_after_sync();
 
-    if (w < kPrepWarps) {
-        // ------------------------------------------------------------------ prep
-        int p = 0;           // pair counter of this CTA
-        unsigned r = 0;      // template counter (ring slot r % kTSlots, use r / kTSlots)
-        unsigned pend = 0u;  // ring slots with a copy issued and not yet waited for
-        const float inv_f = 1.0f / kF;
-        float2 *buf0 = reinterpret_cast<float2 *>(b1);
+    if (w < kMmaWarp0) {
+        // ------------------------------------------------------------------ worker group g
+        const int g = w >> 2, gt = tid & 127;  // group and thread index within the group
+        unsigned char *const region = smem + g * kGroupBytes;  // FFT buffers, then B1 (hi, lo)
+        float2 *const Ws = reinterpret_cast<float2 *>(region + kXBytes);
+        float2 *buf0 = reinterpret_cast<float2 *>(region);
         float2 *buf1 = buf0 + kPadded;
-        for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+        unsigned *const red = reinterpret_cast<unsigned *>(smem + kOffMisc + 16 + 16 * g);  // [4]
+        const uint32_t d1 = tm + kColD1 + 64 * g + lane_base;
+        // Mid role: TMEM lane 32 (w & 3) + lane is D1 row (n2, c). The even lane (c = 0) finishes
+        // template 0 of the pair (it needs the imaginary part from its partner), the odd lane
+        // template 1 (it needs the real part).
+        const int n2 = 16 * (w & 3) + (lane & 15);
+        const int tlm = lane >> 4;
+        const bool odd = tlm != 0;
+        const unsigned char *trow = twt + n2 * kTwRow;
+        const float inv_f = 1.0f / kF;
+        int p = 0;  // pair counter of this group
+        for (int item = blockIdx.x * kGroups + g; item < n_items; item += n_virt) {
             const Item it = jobs.get(item);
             const int n = it.n, t0 = it.t0, t1 = it.t1;
             const int origin = it.s * keep - h;
-            for (int i = 0; i < kTSlots && t0 + i < t1; ++i) {
-                const int rs = (r + i) % kTSlots;
-                if (tid == 0 && !*aborted) load_template(tring + rs * kF, tmpl + (size_t)(t0 + i) * kF, &bars[kBarT + rs]);
-                pend |= 1u << rs;
-            }
-            // The FFT buffers overlap both operand slots: the GEMMs of the last two pairs must be done.
-            if (p >= 1) tc_wait(&bars[kBarB1Empty + ((p - 1) & 1)], ((p - 1) >> 1) & 1, aborted);
-            if (p >= 2) tc_wait(&bars[kBarB1Empty + (p & 1)], ((p - 2) >> 1) & 1, aborted);
-
-            // Forward FFT of the segment: W[q] = DFT(w_s)[tid + 128 q] / F.
-            float2 W[16];
+            const int col0 = it.s * keep - h;
+            // Forward FFT of the segment: W[q] = DFT(w_s)[gt + 128 q] / F, kept in shared memory
+            // (each thread reads back only what it wrote). Region X is free: this group's last
+            // GEMM has completed (its D1 was read).
+            float pscale = 1.f;
             {
-                float2 tw2[16];
-                const int k = tid & 15;
-#pragma unroll
-                for (int q = 0; q < 16; ++q) tw2[q] = __ldg(&wtab[8 * ((k * q) & 255)]);
                 float2 v[16];
+                {
+                    float2 tw2[16];
+                    const int k = gt & 15;
 #pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    const int idx = origin + tid + 128 * q;
-                    v[q] = (idx >= 0 && idx < n) ? __ldg(&it.spec[idx]) : make_float2(0.f, 0.f);
+                    for (int q = 0; q < 16; ++q) tw2[q] = __ldg(&wtab[8 * ((k * q) & 255)]);
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const int idx = origin + gt + 128 * q;
+                        v[q] = (idx >= 0 && idx < n) ? __ldg(&it.spec[idx]) : make_float2(0.f, 0.f);
+                    }
+                    fft_passes_12<false>(v, buf0, buf1, tw2, gt, [] {}, [g] { group_sync(g); });
                 }
-                fft_passes_12<false>(v, buf0, buf1, tw2, tid, [] {}, [] { prep_sync(); });
 #pragma unroll
                 for (int hh = 0; hh < 2; ++hh) {
                     float2 tw3[8];
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) tw3[q] = __ldg(&wtab[(tid + 128 * hh) * q]);
+                    for (int q = 0; q < 8; ++q) tw3[q] = __ldg(&wtab[(gt + 128 * hh) * q]);
                     float2 u[8];
-                    fft_pass_3<false>(u, buf1, tw3, tid + 128 * hh);
+                    fft_pass_3<false>(u, buf1, tw3, gt + 128 * hh);
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) W[2 * q + hh] = make_float2(u[q].x * inv_f, u[q].y * inv_f);
+                    for (int q = 0; q < 8; ++q) v[2 * q + hh] = make_float2(u[q].x * inv_f, u[q].y * inv_f);
                 }
-            }
-            float pscale = 1.f;
-            if (HALF) {
-                float mx = 0.f;
+                if (HALF) {
+                    float mx = 0.f;
 #pragma unroll
-                for (int q = 0; q < 16; ++q) mx = fmaxf(mx, fmaxf(fabsf(W[q].x), fabsf(W[q].y)));
-                const unsigned mb = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(mx));
-                if (lane == 0) red[w] = mb;
-                prep_sync();
-                const unsigned mall = max(max(red[0], red[1]), max(red[2], red[3]));
-                // 2^k with k = 8 - exponent(max component), so that |U| 2^k < 2^14.5.
-                int k = mall ? 8 - ((int)((mall >> 23) & 0xFF) - 127) : 0;
-                k = max(-40, min(40, k));
-                const float s1 = __uint_as_float((unsigned)(k + 127) << 23);
+                    for (int q = 0; q < 16; ++q) mx = fmaxf(mx, fmaxf(fabsf(v[q].x), fabsf(v[q].y)));
+                    const unsigned mb = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(mx));
+                    if (lane == 0) red[w & 3] = mb;
+                    group_sync(g);
+                    const unsigned mall = max(max(red[0], red[1]), max(red[2], red[3]));
+                    // 2^k with k = 8 - exponent(max component), so that |U| 2^k < 2^14.5.
+                    int k = mall ? 8 - ((int)((mall >> 23) & 0xFF) - 127) : 0;
+                    k = max(-40, min(40, k));
+                    const float s1 = __uint_as_float((unsigned)(k + 127) << 23);
 #pragma unroll
-                for (int q = 0; q < 16; ++q) W[q] = make_float2(W[q].x * s1, W[q].y * s1);
-                pscale = __uint_as_float((unsigned)(12 - 2 * k + 127) << 23);
+                    for (int q = 0; q < 16; ++q) v[q] = make_float2(v[q].x * s1, v[q].y * s1);
+                    pscale = __uint_as_float((unsigned)(12 - 2 * k + 127) << 23);
+                }
+#pragma unroll
+                for (int q = 0; q < 16; ++q) Ws[gt + 128 * q] = v[q];
             }
-            prep_sync();  // every prep thread is done with the FFT buffers (and with red[])
+            group_sync(g);  // every thread of the group is done with the FFT buffers (and red[])
+            uint32_t omask = 0u;  // outputs n = 64 n1 + n2 kept (h <= n < h + keep) and inside the spectrum
+#pragma unroll
+            for (int n1 = 0; n1 < 32; ++n1) {
+                const int m = 64 * n1 + n2;
+                if (m >= h && m < h + keep && col0 + m < n) omask |= 1u << n1;
+            }
 
             for (int t = t0; t < t1; t += 2, ++p) {
                 const int tb = min(2, t1 - t);
-                const int s = p & 1;
-                if (p >= 2) tc_wait(&bars[kBarB1Empty + s], ((p - 2) >> 1) & 1, aborted);
-                unsigned char *const slot = b1 + s * kB1Slot;
-                for (int tl = 0; tl < tb; ++tl, ++r) {
-                    const int rs = r % kTSlots;
-                    tc_wait(&bars[kBarT + rs], (r / kTSlots) & 1, aborted);
-                    pend &= ~(1u << rs);
-                    const float2 *T = tring + rs * kF + tid;
+                // prep: U = W T_t; B1 row 32 tl + lane, K chunk 4 (w & 3) + i holds q = 4 i .. 4 i + 3.
+                for (int tl = 0; tl < tb; ++tl) {
+                    const float2 *T = tmpl + (size_t)(t + tl) * kF + gt;
+                    float2 tv[16];
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) tv[q] = __ldg(&T[128 * q]);
                     uint32_t hw[16], lw[16];
 #pragma unroll
                     for (int q = 0; q < 16; ++q) {
-                        const float2 u = cmul(W[q], T[128 * q]);
+                        const float2 u = cmul(Ws[gt + 128 * q], tv[q]);
                         split2<HALF>(u.x, u.y, hw[q], lw[q]);
                     }
-                    // Row 32 tl + lane, K chunk 4 w + i holds q = 4 i .. 4 i + 3.
-                    unsigned char *row = slot + kmajor_off(32 * tl + lane, 32 * w, 2048);
+                    unsigned char *row = region + kmajor_off(32 * tl + lane, 32 * (w & 3), 2048);
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
                         *reinterpret_cast<uint4 *>(row + 128 * i) =
@@ -322,101 +317,36 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         *reinterpret_cast<uint4 *>(row + kB1Term + 128 * i) =
                             make_uint4(lw[4 * i], lw[4 * i + 1], lw[4 * i + 2], lw[4 * i + 3]);
                     }
-                    prep_sync();  // every prep thread has read ring slot rs
-                    if (t + tl + kTSlots < t1) {
-                        if (tid == 0 && !*aborted)
-                            load_template(tring + rs * kF, tmpl + (size_t)(t + tl + kTSlots) * kF, &bars[kBarT + rs]);
-                        pend |= 1u << rs;
-                    }
                 }
-                if (HALF && tid == 0) scale_ring[p & 15] = pscale;
+                tc::fence_before_sync();  // this warp's reads of D1 (previous pair) are done
                 tc::fence_proxy_async();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&bars[kBarB1Full + s]);
-            }
-        }
-        // Copies still in flight (only after an abort) land before the CTA exits.
-        for (int i = 0; i < kTSlots; ++i)
-            if (pend & (1u << i)) {
-                const unsigned ri = r + (unsigned)((i - (int)(r % kTSlots) + kTSlots) % kTSlots);
-                mbar_wait(&bars[kBarT + i], (ri / kTSlots) & 1);
-            }
-    } else if (w == kMmaWarp) {
-        // ------------------------------------------------------------------ MMA issue
-        if (lane == 0) {
-            constexpr uint32_t id1 = tc::idesc_f16(128, 64, !HALF);
-            const uint32_t b1base = smem_u32(b1);
-            int p = 0;
-            for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-                const Item it = jobs.get(item);
-                for (int t = it.t0; t < it.t1; t += 2, ++p) {
-                    const int s = p & 1;
-                    tc_wait(&bars[kBarB1Full + s], (p >> 1) & 1, aborted);
-                    if (p >= 2) tc_wait(&bars[kBarD1Empty + s], ((p - 2) >> 1) & 1, aborted);
-                    if (*aborted) continue;
-                    tc::fence_after_sync();
-                    const uint32_t d1 = tm + kColD1 + 64 * s, bs = b1base + s * kB1Slot;
-#pragma unroll
-                    for (int kk = 0; kk < 8; ++kk) {
-                        const uint64_t bh = tc::desc_kmajor(bs + 256 * kk, 128, 2048);
-                        const uint64_t bl = tc::desc_kmajor(bs + kB1Term + 256 * kk, 128, 2048);
-                        tc::mma_ts(d1, tm + kColAlo + 8 * kk, bh, id1, kk > 0);
-                        tc::mma_ts(d1, tm + kColAhi + 8 * kk, bl, id1, 1u);
-                        tc::mma_ts(d1, tm + kColAhi + 8 * kk, bh, id1, 1u);
-                    }
-                    tc::commit(reinterpret_cast<uint64_t *>(&bars[kBarB1Empty + s]));
-                    tc::commit(reinterpret_cast<uint64_t *>(&bars[kBarD1Full + s]));
-                }
-            }
-        }
-        __syncwarp();
-    } else {
-        // ------------------------------------------------------------------ mid
-        // TMEM lane 32 (w & 3) + lane is D1 row (n2, c). The even lane (c = 0) finishes template 0
-        // of the pair (it needs the imaginary part from its partner), the odd lane template 1 (it
-        // needs the real part).
-        const int n2 = 16 * (w & 3) + (lane & 15);
-        const int tl = lane >> 4;
-        const bool odd = tl != 0;
-        const unsigned char *trow = twt + n2 * kTwRow;
-        int p = 0;
-        for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-            const Item it = jobs.get(item);
-            const int col0 = it.s * keep - h;
-            uint32_t omask = 0u;  // outputs n = 64 n1 + n2 kept (h <= n < h + keep) and inside the spectrum
-#pragma unroll
-            for (int n1 = 0; n1 < 32; ++n1) {
-                const int m = 64 * n1 + n2;
-                if (m >= h && m < h + keep && col0 + m < it.n) omask |= 1u << n1;
-            }
-            for (int t = it.t0; t < it.t1; t += 2, ++p) {
-                const int s = p & 1;
-                tc_wait(&bars[kBarD1Full + s], (p >> 1) & 1, aborted);
+                if (lane == 0) mbar_arrive(&bars[bar_b1full(g)]);
+
+                // mid: wait for the GEMM, then finish both templates of the pair.
+                tc_wait(&bars[bar_d1full(g)], p & 1, aborted);
                 tc::fence_after_sync();
                 float2 v[32];
-                {
-                    uint32_t xe[32], xo[32];  // own component (re if even lane, im if odd) of templates 0, 1
-                    const uint32_t d1 = tm + kColD1 + 64 * s + lane_base;
-                    tc::tmem_ld32(d1, xe);
-                    tc::tmem_ld32(d1 + 32, xo);
-                    tc::fence_before_sync();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&bars[kBarD1Empty + s]);
 #pragma unroll
-                    for (int m1 = 0; m1 < 32; m1 += 2) {
-                        const float ga = __shfl_xor_sync(0xFFFFFFFFu, __uint_as_float(odd ? xe[m1] : xo[m1]), 16);
-                        const float gb = __shfl_xor_sync(0xFFFFFFFFu, __uint_as_float(odd ? xe[m1 + 1] : xo[m1 + 1]), 16);
-                        const float2 da = odd ? make_float2(ga, __uint_as_float(xo[m1])) : make_float2(__uint_as_float(xe[m1]), ga);
-                        const float2 db = odd ? make_float2(gb, __uint_as_float(xo[m1 + 1])) : make_float2(__uint_as_float(xe[m1 + 1]), gb);
+                for (int hh = 0; hh < 2; ++hh) {
+                    uint32_t xe[16], xo[16];  // own component (re if even lane, im if odd) of templates 0, 1
+                    tc::tmem_ld16(d1 + 16 * hh, xe);
+                    tc::tmem_ld16(d1 + 32 + 16 * hh, xo);
+#pragma unroll
+                    for (int i = 0; i < 16; i += 2) {
+                        const int m1 = 16 * hh + i;
+                        const float ga = __shfl_xor_sync(0xFFFFFFFFu, __uint_as_float(odd ? xe[i] : xo[i]), 16);
+                        const float gb = __shfl_xor_sync(0xFFFFFFFFu, __uint_as_float(odd ? xe[i + 1] : xo[i + 1]), 16);
+                        const float2 da = odd ? make_float2(ga, __uint_as_float(xo[i])) : make_float2(__uint_as_float(xe[i]), ga);
+                        const float2 db = odd ? make_float2(gb, __uint_as_float(xo[i + 1])) : make_float2(__uint_as_float(xe[i + 1]), gb);
                         const float4 tw = *reinterpret_cast<const float4 *>(trow + 8 * m1);
                         v[m1] = cmul(da, make_float2(tw.x, tw.y));
                         v[m1 + 1] = cmul(db, make_float2(tw.z, tw.w));
                     }
                 }
                 idft32(v);  // v[n1] = u[64 n1 + n2]
-                if (t + tl < it.t1) {
-                    const float pscale = HALF ? scale_ring[p & 15] : 1.f;
-                    float *const dst = it.plane + (size_t)(t + tl) * it.ld + col0 + n2;
+                if (t + tlm < t1) {
+                    float *const dst = it.plane + (size_t)(t + tlm) * it.ld + col0 + n2;
 #pragma unroll
                     for (int n1 = 0; n1 < 32; ++n1) {
                         const float pw = HALF ? fmaf(v[n1].x, v[n1].x, v[n1].y * v[n1].y) * pscale
@@ -426,15 +356,45 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 }
             }
         }
+    } else {
+        // ------------------------------------------------------------------ MMA issue for group g
+        const int g = w - kMmaWarp0;
+        if (lane == 0) {
+            constexpr uint32_t id1 = tc::idesc_f16(128, 64, !HALF);
+            const uint32_t bs = smem_u32(smem + g * kGroupBytes);
+            const uint32_t d1 = tm + kColD1 + 64 * g;
+            int p = 0;
+            for (int item = blockIdx.x * kGroups + g; item < n_items; item += n_virt) {
+                const Item it = jobs.get(item);
+                for (int t = it.t0; t < it.t1; t += 2, ++p) {
+                    tc_wait(&bars[bar_b1full(g)], p & 1, aborted);
+                    if (*aborted) continue;
+                    tc::fence_after_sync();
+#pragma unroll
+                    for (int kk = 0; kk < 8; ++kk) {
+                        const uint64_t bh = tc::desc_kmajor(bs + 256 * kk, 128, 2048);
+                        const uint64_t bl = tc::desc_kmajor(bs + kB1Term + 256 * kk, 128, 2048);
+                        tc::mma_ts(d1, tm + kColAlo + 8 * kk, bh, id1, kk > 0);
+                        tc::mma_ts(d1, tm + kColAhi + 8 * kk, bl, id1, 1u);
+                        tc::mma_ts(d1, tm + kColAhi + 8 * kk, bh, id1, 1u);
+                    }
+                    tc::commit(reinterpret_cast<uint64_t *>(&bars[bar_d1full(g)]));
+                }
+            }
+        }
+        __syncwarp();
     }
 
     // Teardown: nothing of this CTA may be in flight when its TMEM is freed. Without an abort
-    // every MMA and copy was waited for; after one, wait (bounded) for the MMAs issued.
+    // every MMA was waited for; after one, wait (bounded) for the MMAs each issuer issued.
     tc::fence_before_sync();
     __syncthreads();
     if (*aborted) {
-        if (tid == kMmaWarp * 32) tc::commit(reinterpret_cast<uint64_t *>(&bars[kBarFin]));
-        mbar_wait(&bars[kBarFin], 0u);
+        for (int g = 0; g < kGroups; ++g) {
+            if (tid == (kMmaWarp0 + g) * 32) tc::commit(reinterpret_cast<uint64_t *>(&bars[kBarFin]));
+            mbar_wait(&bars[kBarFin], (unsigned)(g & 1));
+            __syncthreads();
+        }
     }
     tc::fence_before_sync();
     __syncthreads();
