@@ -33,9 +33,19 @@ SM_MAX_MHZ = 2070.0
 # FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 flop (FMA) x 2.07 GHz.
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
 
-# DRAM bytes per launch from the last ncu capture of each kernel, valid only for the source hash given.
-# (kernel source sha256[:12], read+write bytes per N = 2^21 launch)
-NCU_TRAFFIC = {}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the last ncu capture of
+# each kernel at N = 2^21, valid only while the sources it was built from are unchanged:
+# kernel file -> (sha256[:12] of its sources, bytes per fdas_convolve / fdas_harmonic_sum call).
+KERNEL_SOURCES = {
+    "convolve.cu": ("convolve.cu", "ols_common.cuh"),
+    "convolve_tc.cu": ("convolve_tc.cu", "ols_common.cuh", "tc_ops.cuh"),
+    "harmonic.cu": ("harmonic.cu",),
+}
+NCU_TRAFFIC = {
+    "convolve.cu": ("81ae411c08de", 670.7e6),
+    "convolve_tc.cu": ("c7934a72a93f", 669.6e6),
+    "harmonic.cu": ("f0c14a1281da", 1874.6e6),
+}
 
 
 def peaks():
@@ -47,9 +57,21 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def src_hash(name):
-    with open(os.path.join(ROOT, "paper_1806_01556_gb300", "csrc", name), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:12]
+def bf16_peak():
+    """Dense BF16 tensor peak in TFLOP/s (measured cuBLAS burst figure), and its source."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    except Exception:
+        return 1900.0, "fallback"
+
+
+def src_hash(kernel_file):
+    d = hashlib.sha256()
+    for name in KERNEL_SOURCES[kernel_file]:
+        with open(os.path.join(ROOT, "paper_1806_01556_gb300", "csrc", name), "rb") as f:
+            d.update(f.read())
+    return d.hexdigest()[:12]
 
 
 def traffic_for(kernel_file):
@@ -57,6 +79,38 @@ def traffic_for(kernel_file):
     if entry and entry[0] == src_hash(kernel_file):
         return entry[1]
     return None
+
+
+# Convolution forms (fdas_params.precision). The plane error of each against the FP64 oracle is
+# checked by the GPU tests (bar: 1e-4 relative everywhere); this file times them.
+FORMS = {"fp32": 0, "bf16x3": 1, "fp16s": 2}
+TC_TEMPLATES_PER_ITEM = 44  # default work-item size of the tensor-core form (pairs of templates)
+
+
+def hs_launches(n_harm=8, n_temp=85):
+    """Kernel launches of one fdas_harmonic_sum: reset, one per non-empty group of rows (plane
+    counts 5-16, 3-4, 2), the single-plane rows, finalize."""
+    c = (n_temp - 1) // 2
+    groups = 0
+    for kmin, kmax in ((5, 16), (3, 4), (2, 2)):
+        if kmin > n_harm:
+            continue
+        lo = 0 if kmax >= n_harm else c // (kmax + 1) + 1
+        if c // kmin >= lo:
+            groups += 1
+    k1 = 1 if (n_harm < 2 or c // 2 + 1 <= c) else 0
+    return 2 + groups + k1
+
+
+def tc_executed_flop(n, n_temp=85, n_tap=421, fft_len=2048):
+    """Tensor-core flops the split forms execute per spectrum: 24 MMAs (M=128, N=64, K=16) per
+    pair of templates per segment, with templates chunked 44 per work item."""
+    keep = fft_len - n_tap + 1
+    n_seg = -(-n // keep)
+    pairs = 0
+    for t0 in range(0, n_temp, TC_TEMPLATES_PER_ITEM):
+        pairs += -(-min(TC_TEMPLATES_PER_ITEM, n_temp - t0) // 2)
+    return n_seg * pairs * 24 * 2 * 128 * 64 * 16
 
 
 def algorithmic(n, n_temp=85, n_tap=421, fft_len=2048, n_harm=8):
@@ -71,28 +125,41 @@ def algorithmic(n, n_temp=85, n_tap=421, fft_len=2048, n_harm=8):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    """nvidia-smi clocks and throttle reasons sampled every 20 ms from __enter__ to __exit__.
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    begin()/end() mark the timed region; summary() keeps the samples taken in it, widened by
+    0.1 s on each side when the region is shorter than a few sampling periods."""
+
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index):
         self.index = index
         self.proc = None
+        self.t_begin = self.t_end = None
+        self.lines = []
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "20"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            time.sleep(0.3)  # let it start sampling before the timed region
         except Exception:
             self.proc = None
         return self
 
+    def begin(self):
+        self.t_begin = time.time()
+
+    def end(self):
+        self.t_end = time.time()
+
     def __exit__(self, *exc):
         self.lines = []
         if self.proc is not None:
+            time.sleep(0.1)
             self.proc.terminate()
             try:
                 out, _ = self.proc.communicate(timeout=5)
@@ -102,23 +169,48 @@ class ClockSampler:
             self.lines = [ln for ln in out.splitlines() if ln.strip()]
 
     def summary(self):
-        sm, mx, reasons = [], None, set()
+        import datetime
+
+        rows = []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in getattr(self, "lines", []):
+        for ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sm.append(float(f[1]))
-                mx = float(f[2])
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(f[2]), float(f[3]), f[6:10]))
             except ValueError:
                 continue
-            for name, v in zip(names, f[5:9]):
+        lo, hi = self.t_begin, self.t_end
+        window = None
+        if lo is not None and hi is not None:
+            pad = 0.1 if hi - lo < 0.1 else 0.0
+            window = [r for r in rows if lo - pad <= r[0] <= hi + pad]
+        sel = window if window else rows
+        if not sel:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        reasons = set()
+        for r in sel:
+            for name, v in zip(names, r[3]):
                 if v.lower().startswith("active"):
                     reasons.add(name)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+        return {"sm_mhz": statistics.median(r[1] for r in sel), "sm_max_mhz": sel[-1][2], "reasons": sorted(reasons),
+                "samples": len(sel), "window": "timed region" if window else "whole run"}
+
+
+class _Null:
+    def __enter__(self):
+        return self
+
+    def begin(self):
+        pass
+
+    def end(self):
+        pass
+
+    def __exit__(self, *exc):
+        return False
 
 
 def dist_env():
@@ -204,7 +296,7 @@ def workload_config(n):
         "workload": f"SKA-sized spectrum N={n} (2^{int(np.log2(n))}), 4 drifting tones x 8 harmonics in unit "
                     "complex Gaussian noise (seed 1, rank r uses seed 1+r); 85 templates z=-42..42, 421 taps, "
                     "overlap-save F=2048; 8 harmonic planes, 6-sigma thresholds, 200 candidates per plane",
-        "n": n, "n_temp": 85, "n_tap": 421, "fft_len": 2048, "n_harm": 8, "precision": "fp32",
+        "n": n, "n_temp": 85, "n_tap": 421, "fft_len": 2048, "n_harm": 8,
         "l2": "inputs larger than L2: the 713 MB plane is written and read every step",
         "parallelism": "replicas (one spectrum per GPU, no collective)",
     }
@@ -233,19 +325,19 @@ def run_fdas(args):
         sec, desc = cpu_oracle_sample(wl, min(args.n, 1 << 19))
         cpu = {"value": 1.0 / sec, "unit": "spectra/s", "cores": 1, "kind": "oracle", "sample": desc}
 
-    p = fdas.Params()
-    s = fdas.Searcher(p, args.n, device=f"cuda:{local}")
     d_spec = torch.from_numpy(wl.spectrum).to(dev)
     stream = torch.cuda.current_stream(dev)
-    ld = s.ld
+    searchers = {name: fdas.Searcher(fdas.Params(precision=code), args.n, device=f"cuda:{local}")
+                 for name, code in FORMS.items() if name in args.forms}
 
-    def step(ev=None):
+    def step(s, ev=None):
+        p = s.p
         if ev is not None:
             ev[0].record(stream)
-        fdas.fdas_convolve(p, d_spec, args.n, s.tmpl, s.plane, ld, stream)
+        fdas.fdas_convolve(p, d_spec, args.n, s.tmpl, s.plane, s.ld, stream)
         if ev is not None:
             ev[1].record(stream)
-        fdas.fdas_harmonic_sum(p, s.plane, args.n, ld, s.thresh, s.cands, s.counts, s.peaks, s.ws, s.ws_bytes,
+        fdas.fdas_harmonic_sum(p, s.plane, args.n, s.ld, s.thresh, s.cands, s.counts, s.peaks, s.ws, s.ws_bytes,
                                stream)
         if ev is not None:
             ev[2].record(stream)
@@ -254,27 +346,40 @@ def run_fdas(args):
         if world > 1:
             torch.distributed.barrier()
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize(dev)
+    def timed(s, sampler=None):
+        """K steps of one form, bracketed by barrier + synchronize; per-step stage events."""
+        for _ in range(args.warmup):
+            step(s)
+        torch.cuda.synchronize(dev)
+        events = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ctx = sampler if sampler is not None else _Null()
+        with ctx:
+            barrier()
+            torch.cuda.synchronize(dev)
+            ctx.begin()
+            start.record(stream)
+            for k in range(args.steps):
+                step(s, events[k])
+            end.record(stream)
+            torch.cuda.synchronize(dev)
+            ctx.end()
+            barrier()
+        total_ms = max_over_ranks(start.elapsed_time(end), world, dev)
+        return {"total_ms": total_ms,
+                "conv_ms": float(np.mean([e[0].elapsed_time(e[1]) for e in events])),
+                "hs_ms": float(np.mean([e[1].elapsed_time(e[2]) for e in events]))}
 
-    events = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
-    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    sampler = ClockSampler(local)
-    with sampler:
-        barrier()
-        torch.cuda.synchronize(dev)
-        start.record(stream)
-        for k in range(args.steps):
-            step(events[k])
-        end.record(stream)
-        torch.cuda.synchronize(dev)
-        barrier()
-    total_ms = max_over_ranks(start.elapsed_time(end), world, dev)
-    conv_ms = [e[0].elapsed_time(e[1]) for e in events]
-    hs_ms = [e[1].elapsed_time(e[2]) for e in events]
-    ms_per_step = total_ms / args.steps
-    value = job_throughput(world, args.steps, total_ms / 1e3)
+    # The form that goes in "value" is timed with the clock sampler; the others are timed the same way.
+    results, samplers = {}, {}
+    for name, s in searchers.items():
+        samplers[name] = ClockSampler(local)
+        results[name] = timed(s, samplers[name])
+    head = min(results, key=lambda k: results[k]["total_ms"]) if args.headline == "best" else args.headline
+    s = searchers[head]
+    p = s.p
+    ms_per_step = results[head]["total_ms"] / args.steps
+    value = job_throughput(world, args.steps, results[head]["total_ms"] / 1e3)
 
     # End to end through fdas_search_host: pinned host spectrum in, candidates out, every step.
     h_spec = torch.from_numpy(wl.spectrum).pin_memory()
@@ -289,47 +394,68 @@ def run_fdas(args):
 
     if rank == 0:
         alg = algorithmic(args.n)
-        conv_avg = float(np.mean(conv_ms)) / 1e3
-        hs_avg = float(np.mean(hs_ms)) / 1e3
         hbm, hbm_kind = peaks()
-        conv_tflops = alg["conv_flop"] / conv_avg / 1e12
-        hs_gbs = alg["hs_bytes"] / hs_avg / 1e9
-        stages = {
-            "convolve": {"ms": conv_avg * 1e3, "bound": "alu", "achieved": conv_tflops, "unit": "TFLOP/s",
-                         "peak": FP32_PEAK_TFLOPS, "frac": conv_tflops / FP32_PEAK_TFLOPS,
-                         "hbm_gbs": alg["conv_bytes"] / conv_avg / 1e9,
-                         "traffic": traffic_for("convolve.cu")},
-            "harmonic_sum": {"ms": hs_avg * 1e3, "bound": "hbm", "achieved": hs_gbs, "unit": "GB/s", "peak": hbm,
-                             "frac": hs_gbs / hbm, "traffic": traffic_for("harmonic.cu")},
-        }
-        dom = "convolve" if conv_avg >= hs_avg else "harmonic_sum"
-        d = stages[dom]
+        tc_peak, tc_kind = bf16_peak()
+        forms = {}
+        for name, r in results.items():
+            conv_s, hs_s = r["conv_ms"] / 1e3, r["hs_ms"] / 1e3
+            conv_tflops = alg["conv_flop"] / conv_s / 1e12
+            hs_gbs = alg["hs_bytes"] / hs_s / 1e9
+            conv = {"ms": r["conv_ms"], "bound": "alu", "achieved": conv_tflops, "unit": "TFLOP/s",
+                    "peak": FP32_PEAK_TFLOPS, "frac": conv_tflops / FP32_PEAK_TFLOPS,
+                    "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                    "hbm_gbs": alg["conv_bytes"] / conv_s / 1e9,
+                    "traffic": traffic_for("convolve.cu" if name == "fp32" else "convolve_tc.cu")}
+            if name != "fp32":
+                executed = tc_executed_flop(args.n)
+                conv["tensor"] = {"executed_tflops": executed / conv_s / 1e12, "peak": tc_peak,
+                                  "frac": executed / conv_s / 1e12 / tc_peak,
+                                  "peak_source": f"MEASURED_PEAKS.json bf16_tflops ({tc_kind})",
+                                  "note": "MMA flops executed (3 split products, real form) over the kernel time"}
+            forms[name] = {
+                "spectra_per_s": job_throughput(world, args.steps, r["total_ms"] / 1e3),
+                "ms_per_step": r["total_ms"] / args.steps,
+                "stages": {
+                    "convolve": conv,
+                    "harmonic_sum": {"ms": r["hs_ms"], "bound": "hbm", "achieved": hs_gbs, "unit": "GB/s",
+                                     "peak": hbm, "frac": hs_gbs / hbm, "traffic": traffic_for("harmonic.cu"),
+                                     "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({hbm_kind})"},
+                },
+                "clocks": samplers[name].summary(),
+            }
+        st = forms[head]["stages"]
+        dom = "convolve" if st["convolve"]["ms"] >= st["harmonic_sum"]["ms"] else "harmonic_sum"
+        d = st[dom]
         roof = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
-                "frac": d["frac"], "traffic": d["traffic"],
-                "peak_source": ("152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz" if dom == "convolve"
-                                else f"MEASURED_PEAKS.json hbm_gbs ({hbm_kind})")}
+                "frac": d["frac"], "traffic": d["traffic"], "peak_source": d["peak_source"]}
         d2h = p.n_harm * p.cand_cap * 12 + p.n_harm * 4 + p.n_harm * 12
+        cfg = workload_config(args.n)
+        cfg["precision"] = head
         line = {
             "metric": METRIC, "value": value, "unit": "spectra/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(args.n),
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
             "fa_points_per_s": value * 85 * args.n,
-            "clocks": sampler.summary(),
+            "clocks": forms[head]["clocks"],
             "e2e": {"value": job_throughput(world, args.steps, e2e_s), "unit": "spectra/s",
                     "h2d_bytes_per_step": args.n * 8, "d2h_bytes_per_step": d2h},
-            "gpu_launches": 4 * args.steps,
+            "gpu_launches": (1 + hs_launches(p.n_harm, p.n_temp)) * args.steps,
             "roofline": roof,
-            "stages": stages,
+            "stages": st,
+            "forms": forms,
             "cpu_baseline": cpu,
             "candidates_per_plane": [int(c) for c in counts],
         }
+        if "fp32" in forms and "bf16x3" in forms:
+            line["split_bf16_vs_fp32"] = forms["bf16x3"]["spectra_per_s"] / forms["fp32"]["spectra_per_s"]
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
 
 
 def run_batch(args):
-    """Batched form: 64 uneven spectra (2^18..2^22 bins), one plan replayed as a CUDA graph."""
+    """Batched form: 64 uneven spectra (2^18..2^22 bins), one plan replayed as a CUDA graph, for each
+    convolution form in --forms; the fastest goes in value."""
     import torch
 
     import paper_1806_01556_gb300 as fdas
@@ -337,40 +463,50 @@ def run_batch(args):
 
     torch.cuda.set_device(0)
     wls = synth.batch_workloads(args.batch, seed=3)
-    p = fdas.Params()
-    batch = fdas.Batch(p, [w.n for w in wls])
-    for b, w in enumerate(wls):
-        batch.specs[b].copy_(torch.from_numpy(w.spectrum))
-    plan = batch.plan()
-    (ctas, tpi), conv_ms = plan.tune()
-    for _ in range(args.warmup):
-        plan.launch()
-    torch.cuda.synchronize()
-    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    stream = torch.cuda.current_stream()
-    sampler = ClockSampler(0)
-    with sampler:
-        start.record(stream)
-        for _ in range(args.steps):
-            plan.launch()
-        end.record(stream)
-        torch.cuda.synchronize()
-    ms = start.elapsed_time(end) / args.steps
     bins = sum(w.n for w in wls)
+    stream = torch.cuda.current_stream()
+    forms = {}
+    for name in args.forms:
+        p = fdas.Params(precision=FORMS[name])
+        batch = fdas.Batch(p, [w.n for w in wls])
+        for b, w in enumerate(wls):
+            batch.specs[b].copy_(torch.from_numpy(w.spectrum))
+        plan = batch.plan()
+        (ctas, tpi), conv_ms = plan.tune()
+        for _ in range(args.warmup):
+            plan.launch()
+        torch.cuda.synchronize()
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        sampler = ClockSampler(0)
+        with sampler:
+            sampler.begin()
+            start.record(stream)
+            for _ in range(args.steps):
+                plan.launch()
+            end.record(stream)
+            torch.cuda.synchronize()
+            sampler.end()
+        ms = start.elapsed_time(end) / args.steps
+        forms[name] = {"spectra_per_s": len(wls) / (ms / 1e3), "ms_per_step": ms,
+                       "tuned": {"ctas_per_sm": ctas, "templates_per_item": tpi, "conv_ms": conv_ms},
+                       "clocks": sampler.summary(), "gpu_launches_per_step": 1 + hs_launches(p.n_harm, p.n_temp)}
+        plan.close()
+        del batch
+    head = max(forms, key=lambda k: forms[k]["spectra_per_s"])
+    f = forms[head]
     line = {
-        "metric": "FDAS spectra/s, batched uneven spectra", "value": len(wls) / (ms / 1e3), "unit": "spectra/s",
-        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-        "dtype": "f32", "data": "synthetic",
+        "metric": "FDAS spectra/s, batched uneven spectra", "value": f["spectra_per_s"], "unit": "spectra/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": f["ms_per_step"],
+        "higher_is_better": True, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"{len(wls)} dedispersion-trial spectra, lengths floor(2^U), U~Uniform(18,22), seed 3, "
                                "0-3 drifting tones x 8 harmonics each; 85 templates, 421 taps, F=2048, 8 planes",
-                   "total_bins": bins, "launch": "fdas_batch_plan (CUDA graph replay)",
-                   "tuned": {"ctas_per_sm": ctas, "templates_per_item": tpi, "conv_ms": conv_ms}},
-        "fa_points_per_s": 85 * bins / (ms / 1e3),
-        "clocks": sampler.summary(),
-        "gpu_launches": 11 * args.steps,
+                   "total_bins": bins, "launch": "fdas_batch_plan (CUDA graph replay)", "precision": head},
+        "fa_points_per_s": 85 * bins / (f["ms_per_step"] / 1e3),
+        "clocks": f["clocks"],
+        "gpu_launches": f["gpu_launches_per_step"] * args.steps,
+        "forms": forms,
     }
     print(json.dumps(line), flush=True)
-    plan.close()
 
 
 def run_serve(args):
@@ -400,6 +536,7 @@ def run_serve(args):
     sampler = ClockSampler(0)
     done = []
     with sampler:
+        sampler.begin()
         t0 = time.perf_counter()
         t_next = t0
         for k in range(n_req):
@@ -415,6 +552,7 @@ def run_serve(args):
         while len(done) < n_req:
             done += server.poll(256, wait_ms=50)
         t1 = time.perf_counter()
+        sampler.end()
     server.close()
     lat = np.array([r["done_s"] - r["submit_s"] for r in done]) * 1e3
     wait = np.array([r["admit_s"] - r["submit_s"] for r in done]) * 1e3
@@ -435,6 +573,26 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def run_profile(args):
+    """Untimed searches for profiler captures: --steps searches of the SKA workload (args.n bins) with
+    each form in --forms, one after the other. Prints nothing but a status line."""
+    import torch
+
+    import paper_1806_01556_gb300 as fdas
+    import synth
+
+    torch.cuda.set_device(0)
+    wl = synth.ska_workload(n=args.n, seed=1)
+    d_spec = torch.from_numpy(wl.spectrum).cuda()
+    for name in args.forms:
+        s = fdas.Searcher(fdas.Params(precision=FORMS[name]), args.n)
+        for _ in range(args.steps):
+            s.search(d_spec, args.n)
+        torch.cuda.synchronize()
+    print(json.dumps({"mode": "profile", "n": args.n, "forms": args.forms, "searches_per_form": args.steps,
+                      "device_status": fdas.fdas_device_status()}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -443,20 +601,29 @@ def main():
     ap.add_argument("--impl", default="fdas", choices=["fdas", "reference"])
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="single", choices=["single", "batch", "serve"])
+    ap.add_argument("--mode", default="single", choices=["single", "batch", "serve", "profile"])
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--duration", type=float, default=5.0)
     ap.add_argument("--serve-gb", type=int, default=8)
     ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--forms", default="fp32,bf16x3,fp16s",
+                    help="convolution forms to time (comma list of fp32, bf16x3, fp16s)")
+    ap.add_argument("--headline", default="best",
+                    help="form reported in value: best (fastest measured) or one of the forms")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    args.forms = [f for f in args.forms.split(",") if f in FORMS] or ["fp32"]
+    if args.headline != "best" and args.headline not in args.forms:
+        args.forms.append(args.headline)
     if args.impl == "reference":
         run_reference(args)
     elif args.mode == "batch":
         run_batch(args)
     elif args.mode == "serve":
         run_serve(args)
+    elif args.mode == "profile":
+        run_profile(args)
     else:
         run_fdas(args)
 

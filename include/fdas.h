@@ -112,6 +112,14 @@ const char *fdas_status_string(fdas_status s);
 #define FDAS_DEV_WAIT_TIMEOUT 1u
 fdas_status fdas_device_status(uint32_t *flags, int clear);
 
+/* Diagnostic of the bounded-wait path; no counterpart in the paper. Runs, on the current device,
+ * one thread that waits on an mbarrier nothing completes, through the same bounded wait the
+ * convolution kernels use. The wait gives up after about one second and the kernel returns.
+ * *flags receives the device status bits that this left (FDAS_DEV_WAIT_TIMEOUT expected). The
+ * status word is cleared before and after. Synchronous: it waits for the device to go idle.
+ * Returns FDAS_ERR_INVALID_ARG for a null flags, FDAS_ERR_CUDA if a CUDA call fails. */
+fdas_status fdas_check_wait_timeout(uint32_t *flags);
+
 /* Size of the template bank written by fdas_make_templates: (n_temp + 1) * fft_len * 8 bytes.
  * Returns 0 for invalid parameters. */
 size_t fdas_templates_bytes(const fdas_params *p);

@@ -25,6 +25,7 @@ __all__ = [
     "lib",
     "fdas_check_params",
     "fdas_device_status",
+    "fdas_check_wait_timeout",
     "fdas_templates_bytes",
     "fdas_plane_bytes",
     "fdas_workspace_bytes",
@@ -108,6 +109,13 @@ def fdas_device_status(clear: bool = False) -> int:
     """Device status bits of the current device (FDAS_DEV_WAIT_TIMEOUT: a bounded wait gave up)."""
     flags = C.c_uint32(0)
     _check(lib().fdas_device_status(C.byref(flags), int(clear)), "fdas_device_status")
+    return flags.value
+
+
+def fdas_check_wait_timeout() -> int:
+    """Runs the bounded-wait diagnostic (about one second); returns the status bits it left."""
+    flags = C.c_uint32(0)
+    _check(lib().fdas_check_wait_timeout(C.byref(flags)), "fdas_check_wait_timeout")
     return flags.value
 
 

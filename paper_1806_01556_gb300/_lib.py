@@ -85,6 +85,7 @@ SIGNATURES = {
     "fdas_check_params": (C.c_int, [P]),
     "fdas_status_string": (C.c_char_p, [C.c_int]),
     "fdas_device_status": (C.c_int, [C.POINTER(C.c_uint32), C.c_int]),
+    "fdas_check_wait_timeout": (C.c_int, [C.POINTER(C.c_uint32)]),
     "fdas_templates_bytes": (SZ, [P]),
     "fdas_plane_bytes": (SZ, [P, SZ, SZ]),
     "fdas_workspace_bytes": (SZ, [P, SZ]),

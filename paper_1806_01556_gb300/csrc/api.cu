@@ -95,6 +95,14 @@ fdas_status fdas_device_status(uint32_t *flags, int clear) {
     return FDAS_OK;
 }
 
+fdas_status fdas_check_wait_timeout(uint32_t *flags) {
+    if (!flags) return FDAS_ERR_INVALID_ARG;
+    unsigned v = 0u;
+    if (fdas::check_wait_timeout(&v) != cudaSuccess) return FDAS_ERR_CUDA;
+    *flags = v;
+    return FDAS_OK;
+}
+
 size_t fdas_templates_bytes(const fdas_params *p) {
     if (fdas_check_params(p) == FDAS_ERR_INVALID_ARG) return 0;
     return (size_t)(p->n_temp + 1) * (size_t)p->fft_len * 8u;

@@ -179,6 +179,34 @@ cudaError_t launch_convolve_fp32(const Geometry &g, const float2 *spec, size_t n
     return cudaGetLastError();
 }
 
+namespace {
+__device__ unsigned g_wait_check_ok;
+
+// One thread waits on an mbarrier that nothing will ever complete, through the same bounded wait
+// the convolution kernels use. The wait gives up after about one second, records it in the
+// status word and returns; g_wait_check_ok receives 0 then (1 would mean the phase completed).
+__global__ void fdas_wait_timeout_check() {
+    __shared__ unsigned long long bar;
+    mbar_init(&bar);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    g_wait_check_ok = mbar_wait(&bar, 0u) ? 1u : 0u;
+}
+}  // namespace
+
+cudaError_t check_wait_timeout(unsigned *flags) {
+    unsigned h_ok = 1u;
+    cudaError_t e = device_status(flags, true);  // start from a clear word
+    if (e == cudaSuccess) {
+        fdas_wait_timeout_check<<<1, 1>>>();
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(&h_ok, g_wait_check_ok, sizeof(unsigned));
+    if (e == cudaSuccess) e = device_status(flags, true);
+    if (e == cudaSuccess && h_ok != 0u) *flags = 0u;  // the phase cannot complete: report no timeout seen
+    return e;
+}
+
 cudaError_t launch_convolve(const Geometry &g, const float2 *spec, size_t n, const float2 *tmpl, float *plane,
                             size_t ld, int ctas_per_sm, int templates_per_item, cudaStream_t s) {
     if (g.precision == FDAS_FP32)

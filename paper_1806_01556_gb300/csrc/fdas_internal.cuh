@@ -106,6 +106,8 @@ cudaError_t device_status_tc(unsigned *flags, bool clear);
 inline int convolve_ctas_per_sm(const Geometry &g) { return g.precision == FDAS_FP32 ? 3 : kTcMaxCtasPerSm; }
 // Status bits set by kernels on the device (bit 0: a bounded wait timed out); optionally cleared.
 cudaError_t device_status(unsigned *flags, bool clear);
+// Runs a kernel whose bounded wait must give up; returns the status bits it left (then cleared).
+cudaError_t check_wait_timeout(unsigned *flags);
 // Batched convolution: one persistent launch over every segment of every spectrum.
 cudaError_t prepare_convolve_batch();
 int convolve_items(const Geometry &g, size_t n, int templates_per_item);

@@ -125,6 +125,7 @@ def test_bad_pointers_are_rejected_before_any_launch(fd):
     assert lib.fdas_default_thresholds(C.byref(p), 6.0, 2, fake) == -1
     assert lib.fdas_status_string(-3) == b"workspace too small"
     assert lib.fdas_device_status(None, 0) == -1
+    assert lib.fdas_check_wait_timeout(None) == -1
 
 
 class _NullStream:
@@ -206,3 +207,35 @@ def test_server_arguments_are_checked_on_the_host(fd):
     want = up(8 * n) + up(85 * ((n + 63) // 64 * 64) * 4) + up(fd.fdas_workspace_bytes(q, n)) + up(8 * 200 * 12) \
         + up(8 * 4) + up(8 * 12)
     assert fd.Server.request_bytes(q, n) == want
+
+
+def test_bench_launch_count_follows_the_row_groups():
+    """bench.py counts the harmonic-sum launches: reset, one per non-empty row group, single-plane rows, finalize."""
+    import bench
+
+    assert bench.hs_launches(8, 85) == 6
+    assert bench.hs_launches(16, 85) == 6
+    assert bench.hs_launches(2, 85) == 4
+    assert bench.hs_launches(1, 85) == 3
+
+
+def test_clock_sampler_keeps_the_timed_window():
+    """bench.py's clock summary uses the nvidia-smi samples taken inside the timed region."""
+    import datetime
+
+    import bench
+
+    cs = bench.ClockSampler(0)
+    t0 = datetime.datetime(2026, 1, 1, 12, 0, 0).timestamp()
+
+    def line(dt, mhz, power_cap="Not Active"):
+        ts = datetime.datetime.fromtimestamp(t0 + dt).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+        return f"{ts}, 0, {mhz}, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, {power_cap}"
+
+    cs.lines = [line(0.0, 1000), line(1.0, 2070), line(1.02, 2070, "Active"), line(1.04, 2070), line(3.0, 1200)]
+    cs.t_begin, cs.t_end = t0 + 0.9, t0 + 1.5
+    s = cs.summary()
+    assert s["samples"] == 3 and s["sm_mhz"] == 2070.0 and s["reasons"] == ["sw_power_cap"]
+    assert s["window"] == "timed region"
+    cs.t_begin, cs.t_end = t0 + 5.0, t0 + 5.01  # nothing inside: the whole run is reported
+    assert cs.summary()["window"] == "whole run"

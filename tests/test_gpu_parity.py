@@ -300,3 +300,25 @@ def test_no_bounded_wait_gave_up(fd, small_case):
     torch.cuda.synchronize()
     assert fd.fdas_device_status(clear=True) == 0
     assert fd.fdas_device_status() == 0
+
+
+def test_bounded_wait_gives_up_and_the_context_stays_usable(fd, small_case):
+    """A wait on an mbarrier nothing completes ends after about a second with the status bit set;
+    the next convolution runs normally and leaves the status clear."""
+    import time
+
+    t0 = time.perf_counter()
+    flags = fd.fdas_check_wait_timeout()
+    dt = time.perf_counter() - t0
+    assert flags & 1
+    assert 0.2 < dt < 30.0
+    assert fd.fdas_device_status() == 0  # cleared by the diagnostic
+    wl, ref = small_case
+    p = fd.Params()
+    s = fd.Searcher(p, wl.n)
+    s.search(torch.from_numpy(wl.spectrum).cuda(), wl.n)
+    torch.cuda.synchronize()
+    got = s.plane[:, : wl.n].cpu().numpy()
+    mx, _ = plane_rel(got, ref)
+    assert mx <= REL_TOL
+    assert fd.fdas_device_status() == 0
