@@ -38,8 +38,9 @@ fdas_status check_items(const fdas_params *p, const fdas_batch_item *items, int 
 struct Tables {
     ConvBatch conv;
     HsBatch hs;
-    int total_kl;
-    int total_k1;
+    int total_16k;  // harmonic-sum CTAs of all spectra in launches of 16384, 8192 and 4096 columns
+    int total_8k;
+    int total_4k;
 };
 
 void build_tables(const fdas_params &p, const fdas_batch_item *items, int count, void *d_ws, int templates_per_item,
@@ -47,7 +48,7 @@ void build_tables(const fdas_params &p, const fdas_batch_item *items, int count,
     const fdas::Geometry g = fdas::geometry(p);
     const size_t stride = hs_ws_stride(p);
     t->conv.count = t->hs.count = count;
-    int item = 0, blk = 0, blk1 = 0;
+    int item = 0, blk = 0, blk1 = 0, blk2 = 0;
     for (int b = 0; b < count; ++b) {
         const fdas_batch_item &it = items[b];
         fdas::ConvJob &cj = t->conv.job[b];
@@ -63,11 +64,12 @@ void build_tables(const fdas_params &p, const fdas_batch_item *items, int count,
         hj.n = (int)it.n;
         hj.blk0 = blk;
         hj.blk1 = blk1;
-        hj.pad = 0;
-        int bk, bk1;
-        fdas::harmonic_blocks(p, it.n, &bk, &bk1);
+        hj.blk2 = blk2;
+        int bk2, bk, bk1;
+        fdas::harmonic_blocks(p, it.n, &bk2, &bk, &bk1);
         blk += bk;
         blk1 += bk1;
+        blk2 += bk2;
         const fdas::HsWorkspace ws = fdas::hs_workspace(static_cast<char *>(d_ws) + (size_t)b * stride, p.n_harm);
         hj.counters = ws.counters;
         hj.peaks = ws.peaks;
@@ -77,8 +79,9 @@ void build_tables(const fdas_params &p, const fdas_batch_item *items, int count,
         hj.peak_out = it.d_peaks;
     }
     t->conv.total_items = item;
-    t->total_kl = blk;
-    t->total_k1 = blk1;
+    t->total_16k = blk2;
+    t->total_8k = blk;
+    t->total_4k = blk1;
 }
 
 cudaError_t sm_count(int *sms) {
@@ -105,7 +108,7 @@ cudaError_t launch_batch(const fdas_params &p, const Tables &t, const void *d_tm
     cudaError_t e = fdas::launch_convolve_batch(g, t.conv, static_cast<const float2 *>(d_tmpl), grid,
                                                 cfg.templates_per_item, s);
     if (e != cudaSuccess || conv_only) return e;
-    return fdas::launch_harmonic_batch(p, t.hs, t.total_kl, t.total_k1, d_thresh, s);
+    return fdas::launch_harmonic_batch(p, t.hs, t.total_16k, t.total_8k, t.total_4k, d_thresh, s);
 }
 
 }  // namespace

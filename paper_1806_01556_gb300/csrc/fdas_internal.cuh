@@ -73,7 +73,7 @@ struct HsJob {
     int n;
     int blk0;   // first CTA of this spectrum in harmonic-sum launches of 8192-column CTAs
     int blk1;   // first CTA of this spectrum in harmonic-sum launches of 4096-column CTAs
-    int pad;
+    int blk2;   // first CTA of this spectrum in harmonic-sum launches of 16384-column CTAs
     unsigned long long *counters;  // this spectrum's workspace (HsWorkspace)
     unsigned long long *peaks;
     unsigned long long *raw;
@@ -117,9 +117,9 @@ cudaError_t launch_harmonic(const fdas_params &p, const float *plane, size_t n, 
                             const float *thresh, fdas_cand *cands, uint32_t *counts, fdas_cand *peaks,
                             const HsWorkspace &ws, cudaStream_t s);
 // Batched harmonic sum: reset, one launch per group of rows over every spectrum, finalize.
-void harmonic_blocks(const fdas_params &p, size_t n, int *blocks_wide, int *blocks_narrow);
+void harmonic_blocks(const fdas_params &p, size_t n, int *blocks_16k, int *blocks_8k, int *blocks_4k);
 cudaError_t prepare_harmonic_batch();
-cudaError_t launch_harmonic_batch(const fdas_params &p, const HsBatch &batch, int total_kl, int total_k1,
-                                  const float *thresh, cudaStream_t s);
+cudaError_t launch_harmonic_batch(const fdas_params &p, const HsBatch &batch, int total_16k, int total_8k,
+                                  int total_4k, const float *thresh, cudaStream_t s);
 
 }  // namespace fdas

@@ -155,9 +155,11 @@ __device__ __forceinline__ int term_count(int j, int n) {
 // warp's chunk has the same number T of terms, which holds for all warps but those straddling a
 // boundary j = (n-1)/l.
 constexpr int kChunks = 8;
-// Fundamentals per thread and chunk: fewer for many planes, to keep the gathers in registers.
+// Fundamentals per thread and chunk: more for few planes (more gathers in flight per thread: the
+// 2- and 4-plane launches went from 0.166 to 0.126 ms at N = 2^21 with 8 instead of 4), fewer for
+// many planes, to keep the gathers in registers.
 template <int KL>
-__host__ __device__ constexpr int jpt() { return KL <= 9 ? 4 : 2; }
+__host__ __device__ constexpr int jpt() { return KL <= 4 ? 8 : KL <= 9 ? 4 : 2; }
 
 template <int KL, bool UNIFORM>
 __device__ __forceinline__ void hs_chunk(const float *const (&rp)[KL], const float (&ta)[KL], int n, int row,
@@ -302,7 +304,9 @@ HsKernel hs_kernel(int kmax) {
         default: return fdas_hs_kl<16>;
     }
 }
-constexpr int kl_width(int kmax) { return kl_size(kmax) <= 8 ? jpt<8>() : jpt<16>(); }
+constexpr int kl_width(int kmax) {
+    return kl_size(kmax) == 2 ? jpt<2>() : kl_size(kmax) == 4 ? jpt<4>() : kl_size(kmax) == 8 ? jpt<8>() : jpt<16>();
+}
 
 // Row groups of the harmonic sum for rows with at least two planes: [kmin, kmax] ranges of
 // klast = min(n_harm, floor(c/|i|)), each launched once. Rows with few planes keep their own,
@@ -389,13 +393,18 @@ __global__ void __launch_bounds__(kFinThreads)
 
 // ---- batched forms: one launch per stage for every spectrum of a batch ----------------------------
 
-// Spectrum of CTA x: the last job whose first CTA (field blk0 or blk1) is <= x.
-template <bool K1>
+// Spectrum of CTA x in a launch of W columns per CTA: the last job whose first CTA in such launches
+// (blk2 for 16384 columns, blk0 for 8192, blk1 for 4096) is <= x.
+template <int W>
+__device__ __forceinline__ int first_block(const HsJob &J) {
+    return W == 16384 ? J.blk2 : W == 8192 ? J.blk0 : J.blk1;
+}
+template <int W>
 __device__ __forceinline__ int job_of_block(const HsBatch &B, int x) {
     int lo = 0, hi = B.count - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        const int first = K1 ? B.job[mid].blk1 : B.job[mid].blk0;
+        const int first = first_block<W>(B.job[mid]);
         if (first <= x) lo = mid; else hi = mid - 1;
     }
     return lo;
@@ -412,7 +421,7 @@ __global__ void fdas_hs_reset_batch(const HsBatch B, int n_harm) {
 
 __global__ void __launch_bounds__(kHsThreads, 4)
     fdas_hs_k1_batch(const HsBatch B, const float *__restrict__ thresh, int n_temp, unsigned mask, int lo) {
-    const HsJob &J = B.job[job_of_block<true>(B, blockIdx.x)];
+    const HsJob &J = B.job[job_of_block<kK1Cols>(B, blockIdx.x)];
     const int c = (n_temp - 1) / 2;
     const int row = c + group_row_offset(blockIdx.y, lo);
     const float ta = (mask & 1u) ? __ldg(&thresh[row]) : __int_as_float(0x7f800000);
@@ -421,19 +430,19 @@ __global__ void __launch_bounds__(kHsThreads, 4)
               vec);
 }
 
-// CTA widths: 8192 columns (kernels for up to 8 terms) or 4096 (16 terms, and the single-plane rows).
-// HsJob.blk0 / blk1 are the spectrum's first CTA in launches of each width.
+// CTA widths: 16384 columns (kernels for up to 4 terms), 8192 (up to 8) or 4096 (16 terms, and the
+// single-plane rows). HsJob.blk2 / blk0 / blk1 are the spectrum's first CTA in launches of each width.
 template <int KL>
 __global__ void __launch_bounds__(kHsThreads, KL <= 3 ? 4 : 2)
     fdas_hs_kl_batch(const HsBatch B, const float *__restrict__ thresh, int n_temp, unsigned mask, int n_harm, int lo) {
-    constexpr bool wide = jpt<KL>() == 4;
-    const HsJob &J = B.job[job_of_block<!wide>(B, blockIdx.x)];
+    constexpr int W = kChunks * kHsThreads * jpt<KL>();
+    const HsJob &J = B.job[job_of_block<W>(B, blockIdx.x)];
     const int c = (n_temp - 1) / 2;
     const int i = group_row_offset(blockIdx.y, lo);
     const int ai = i < 0 ? -i : i;
     const int klast = ai == 0 ? n_harm : min(n_harm, c / ai);
     hs_row<KL>(J.plane, J.n, (size_t)J.ld, thresh, n_temp, mask, c, i, klast,
-               (blockIdx.x - (wide ? J.blk0 : J.blk1)) * (kChunks * kHsThreads * jpt<KL>()), J.raw, J.counters,
+               (blockIdx.x - first_block<W>(J)) * W, J.raw, J.counters,
                J.peaks);
 }
 
@@ -492,14 +501,17 @@ cudaError_t launch_harmonic(const fdas_params &p, const float *plane, size_t n, 
     return cudaGetLastError();
 }
 
-// CTAs of one spectrum of n bins in the launches of rows with K >= 2 planes (all groups use the same
-// column width for n_harm <= 9) and in the launch of single-plane rows.
-void harmonic_blocks(const fdas_params &p, size_t n, int *blocks_wide, int *blocks_narrow) {
+// CTAs of one spectrum of n bins in launches of 16384, 8192 and 4096 columns per CTA (rows with up to
+// 4, up to 8 and 16 planes; the single-plane rows use 4096 too).
+void harmonic_blocks(const fdas_params &p, size_t n, int *blocks_16k, int *blocks_8k, int *blocks_4k) {
     (void)p;
-    const int wide = kChunks * kHsThreads * jpt<8>();  // 8192 columns
-    static_assert(kChunks * kHsThreads * jpt<16>() == kK1Cols, "narrow CTAs of both kinds cover 4096 columns");
-    *blocks_wide = (int)((n + wide - 1) / wide);
-    *blocks_narrow = (int)((n + kK1Cols - 1) / kK1Cols);
+    static_assert(kChunks * kHsThreads * jpt<2>() == 16384 && kChunks * kHsThreads * jpt<4>() == 16384,
+                  "rows with up to 4 planes: 16384 columns per CTA");
+    static_assert(kChunks * kHsThreads * jpt<8>() == 8192, "rows with up to 8 planes: 8192 columns per CTA");
+    static_assert(kChunks * kHsThreads * jpt<16>() == kK1Cols, "16 planes and single-plane rows: 4096 columns");
+    *blocks_16k = (int)((n + 16383) / 16384);
+    *blocks_8k = (int)((n + 8191) / 8192);
+    *blocks_4k = (int)((n + kK1Cols - 1) / kK1Cols);
 }
 
 cudaError_t prepare_harmonic_batch() {
@@ -507,7 +519,7 @@ cudaError_t prepare_harmonic_batch() {
                                 FDAS_RAW_CAP * (int)sizeof(unsigned long long));
 }
 
-cudaError_t launch_harmonic_batch(const fdas_params &p, const HsBatch &B, int total_kl, int total_k1,
+cudaError_t launch_harmonic_batch(const fdas_params &p, const HsBatch &B, int total_16k, int total_8k, int total_4k,
                                   const float *thresh, cudaStream_t s) {
     fdas_hs_reset_batch<<<B.count, 32, 0, s>>>(B, p.n_harm);
     cudaError_t e = cudaGetLastError();
@@ -519,7 +531,8 @@ cudaError_t launch_harmonic_batch(const fdas_params &p, const HsBatch &B, int to
         if (!group_rows(c, p.n_harm, gr.kmin, gr.kmax, &lo, &hi)) continue;
         const int kmax = gr.kmax < p.n_harm ? gr.kmax : p.n_harm;
         const int rows = (lo == 0) ? 2 * hi + 1 : 2 * (hi - lo + 1);
-        const unsigned gx = (unsigned)(kl_width(kmax) == jpt<8>() ? total_kl : total_k1);
+        const int w = kChunks * kHsThreads * kl_width(kmax);
+        const unsigned gx = (unsigned)(w == 16384 ? total_16k : w == 8192 ? total_8k : total_4k);
         hs_batch_kernel(kmax)<<<dim3(gx, (unsigned)rows), kHsThreads, 0, s>>>(B, thresh, p.n_temp, p.harm_mask,
                                                                              p.n_harm, lo);
         e = cudaGetLastError();
@@ -527,7 +540,7 @@ cudaError_t launch_harmonic_batch(const fdas_params &p, const HsBatch &B, int to
     }
     const int rows1 = lo1 == 0 ? 2 * c + 1 : 2 * (c - lo1 + 1);
     if (rows1 > 0) {
-        fdas_hs_k1_batch<<<dim3((unsigned)total_k1, (unsigned)rows1), kHsThreads, 0, s>>>(B, thresh, p.n_temp,
+        fdas_hs_k1_batch<<<dim3((unsigned)total_4k, (unsigned)rows1), kHsThreads, 0, s>>>(B, thresh, p.n_temp,
                                                                                         p.harm_mask, lo1);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
