@@ -336,6 +336,86 @@ __device__ __forceinline__ fdas_cand decode_cand(unsigned long long key, int c, 
     return r;
 }
 
+// One bitonic step of stride S < E between a thread's own keys (index base + e).
+template <int E, int S>
+__device__ __forceinline__ void fin_reg_step(unsigned long long (&r)[E], int base, int size) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        if ((e & S) != 0) continue;
+        const bool up = ((base + e) & size) == 0;
+        const unsigned long long a = r[e], b = r[e + S];
+        const bool sw = (a > b) == up;
+        r[e] = sw ? b : a;
+        r[e + S] = sw ? a : b;
+    }
+}
+
+// Ascending bitonic sort of the nr keys at src, padded with ~0 to np2 = 32 E 2^m >= nr, with E keys
+// per thread: thread t holds keys [E t, E t + E) in registers. Strides below E are exchanges inside
+// a thread, strides E..16 E warp shuffles, and only strides >= 32 E go through shared memory.
+// The first nout keys are decoded to candidates of plane k.
+template <int E>
+__device__ __forceinline__ void fin_sort(const unsigned long long *__restrict__ src, int nr, int np2, int nout, int c,
+                                         int k, int cand_cap, fdas_cand *cands, unsigned long long *keys) {
+    const int nthr = np2 / E;  // active threads, whole warps
+    const bool active = (int)threadIdx.x < nthr;
+    const int base = (int)threadIdx.x * E;
+    const int lane = threadIdx.x & 31;
+    unsigned long long r[E];
+    if (active) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) r[e] = base + e < nr ? src[base + e] : ~0ull;
+    }
+    for (int size = 2; size <= np2; size <<= 1) {
+        if ((size >> 1) >= 32 * E) {
+            if (active) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) keys[base + e] = r[e];
+            }
+            __syncthreads();
+            for (int stride = size >> 1; stride >= 32 * E; stride >>= 1) {
+                for (int x = threadIdx.x; x < (np2 >> 1); x += blockDim.x) {
+                    const int lo = 2 * x - (x & (stride - 1));
+                    const int hi = lo + stride;
+                    const bool up = (lo & size) == 0;
+                    const unsigned long long a = keys[lo], b = keys[hi];
+                    if ((a > b) == up) {
+                        keys[lo] = b;
+                        keys[hi] = a;
+                    }
+                }
+                __syncthreads();
+            }
+            if (active) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) r[e] = keys[base + e];
+            }
+            __syncthreads();  // every read done before the next writes
+        }
+        if (active) {
+            for (int stride = min(size >> 1, 16 * E); stride >= E; stride >>= 1) {
+                const int lx = stride / E;            // partner lane distance
+                const bool lower = (lane & lx) == 0;  // this thread holds the lower index of each pair
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const unsigned long long o = __shfl_xor_sync(0xFFFFFFFFu, r[e], lx);
+                    const bool up = ((base + e) & size) == 0;
+                    r[e] = (lower == up) ? (r[e] < o ? r[e] : o) : (r[e] > o ? r[e] : o);
+                }
+            }
+            if (E > 8 && size >= 16) fin_reg_step<E, (E > 8 ? 8 : 0)>(r, base, size);
+            if (E > 4 && size >= 8) fin_reg_step<E, (E > 4 ? 4 : 0)>(r, base, size);
+            if (E > 2 && size >= 4) fin_reg_step<E, (E > 2 ? 2 : 0)>(r, base, size);
+            fin_reg_step<E, 1>(r, base, size);
+        }
+    }
+    if (active) {
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+            if (base + e < nout) cands[(size_t)(k - 1) * cand_cap + base + e] = decode_cand(r[e], c, k);
+    }
+}
+
 // Counts, peak and the top cand_cap candidates of plane k, from its workspace.
 __device__ __forceinline__ void finalize_plane(int k, const unsigned long long *__restrict__ raw,
                                                const unsigned long long *counters, const unsigned long long *peaks,
@@ -359,28 +439,17 @@ __device__ __forceinline__ void finalize_plane(int k, const unsigned long long *
         }
     }
     if (nr == 0) return;
-    int np2 = 1;
-    while (np2 < nr) np2 <<= 1;
-    const unsigned long long *src = raw + (size_t)(k - 1) * FDAS_RAW_CAP;
-    for (int x = threadIdx.x; x < np2; x += blockDim.x) keys[x] = x < nr ? src[x] : ~0ull;
-    __syncthreads();
-    for (int size = 2; size <= np2; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int x = threadIdx.x; x < (np2 >> 1); x += blockDim.x) {
-                const int lo = 2 * x - (x & (stride - 1));
-                const int hi = lo + stride;
-                const bool up = (lo & size) == 0;
-                const unsigned long long a = keys[lo], b = keys[hi];
-                if ((a > b) == up) {
-                    keys[lo] = b;
-                    keys[hi] = a;
-                }
-            }
-            __syncthreads();
-        }
-    }
     const int nout = nr < cand_cap ? nr : cand_cap;
-    for (int x = threadIdx.x; x < nout; x += blockDim.x) cands[(size_t)(k - 1) * cand_cap + x] = decode_cand(keys[x], c, k);
+    const unsigned long long *src = raw + (size_t)(k - 1) * FDAS_RAW_CAP;
+    // Keys per thread: 2 up to 2048 keys, 4 up to 4096, 16 up to FDAS_RAW_CAP (1024 threads).
+    int np2 = 64;
+    while (np2 < nr) np2 <<= 1;
+    if (np2 <= 2048)
+        fin_sort<2>(src, nr, np2, nout, c, k, cand_cap, cands, keys);
+    else if (np2 <= 4096)
+        fin_sort<4>(src, nr, np2, nout, c, k, cand_cap, cands, keys);
+    else
+        fin_sort<16>(src, nr, np2, nout, c, k, cand_cap, cands, keys);
 }
 
 __global__ void __launch_bounds__(kFinThreads)
