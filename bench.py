@@ -37,14 +37,18 @@ FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
 # each kernel at N = 2^21, valid only while the sources it was built from are unchanged:
 # kernel file -> (sha256[:12] of its sources, bytes per fdas_convolve / fdas_harmonic_sum call).
 KERNEL_SOURCES = {
-    "convolve.cu": ("convolve.cu", "ols_common.cuh"),
+    "convolve.cu": ("convolve.cu", "ols_common.cuh", "hs_keys.cuh"),
     "convolve_tc.cu": ("convolve_tc.cu", "ols_common.cuh", "tc_ops.cuh"),
-    "harmonic.cu": ("harmonic.cu",),
+    "harmonic.cu": ("harmonic.cu", "hs_keys.cuh"),
+    "harmonic.cu+k1": ("harmonic.cu", "hs_keys.cuh"),
 }
+# "harmonic.cu": the harmonic stage of an FP32 search (no single-plane launch); "harmonic.cu+k1":
+# the full harmonic sum, as the tensor-core forms run it.
 NCU_TRAFFIC = {
-    "convolve.cu": ("d8df05041cf2", 670.8e6),
-    "convolve_tc.cu": ("c7934a72a93f", 670.0e6),
-    "harmonic.cu": ("6a778eb8b0db", 1877.6e6),
+    "convolve.cu": ("9a245990738a", 773.1e6),
+    "convolve_tc.cu": ("c7934a72a93f", 669.6e6),
+    "harmonic.cu": ("c17adbf12c34", 1487.3e6),
+    "harmonic.cu+k1": ("c17adbf12c34", 1840.5e6),
 }
 
 
@@ -102,6 +106,22 @@ def hs_launches(n_harm=8, n_temp=85):
     return 2 + groups + k1
 
 
+def search_launches(precision, n_harm=8, n_temp=85):
+    """Kernel launches of one fdas_search (its two stages). FP32 takes HP_1 in the convolution, so
+    its launches are reset, convolution, the row groups and finalize: as many as a harmonic sum
+    alone. The tensor-core forms: reset, convolution, then the whole harmonic sum."""
+    return hs_launches(n_harm, n_temp) + (0 if precision == "fp32" else 2)
+
+
+def hs_rows(precision, n_harm=8, n_temp=85):
+    """Plane rows the harmonic stage of fdas_search reads: with FP32 the single-plane rows are done
+    in the convolution, so only the rows with two or more planes (|i| <= c/2) are read again."""
+    c = (n_temp - 1) // 2
+    if precision == "fp32" and n_harm >= 2:
+        return 2 * (c // 2) + 1
+    return n_temp if precision != "fp32" else 0
+
+
 def tc_executed_flop(n, n_temp=85, n_tap=421, fft_len=2048):
     """Tensor-core flops the split forms execute per spectrum: 24 MMAs (M=128, N=64, K=16) per
     pair of templates per segment, with templates chunked 44 per work item."""
@@ -113,14 +133,15 @@ def tc_executed_flop(n, n_temp=85, n_tap=421, fft_len=2048):
     return n_seg * pairs * 24 * 2 * 128 * 64 * 16
 
 
-def algorithmic(n, n_temp=85, n_tap=421, fft_len=2048, n_harm=8):
-    """Algorithmic work of one spectrum (nominal FFT count 5 F log2 F per transform)."""
+def algorithmic(n, n_temp=85, n_tap=421, fft_len=2048, n_harm=8, rows_read=None):
+    """Algorithmic work of one spectrum (nominal FFT count 5 F log2 F per transform). The harmonic
+    stage reads each plane point of its rows once (rows_read, all rows by default)."""
     keep = fft_len - n_tap + 1
     n_seg = -(-n // keep)
     fft_flop = 5 * fft_len * int(np.log2(fft_len))
     conv_flop = fft_flop * n_seg * (1 + n_temp) + 6 * fft_len * n_seg * n_temp + 3 * n_temp * n
     conv_bytes = n_seg * fft_len * 8 + n_temp * n * 4  # segment reads (with overlap) + plane write
-    hs_bytes = n_temp * n * 4  # every plane point read once
+    hs_bytes = (n_temp if rows_read is None else rows_read) * n * 4
     return dict(conv_flop=conv_flop, conv_bytes=conv_bytes, hs_bytes=hs_bytes, n_seg=n_seg)
 
 
@@ -331,14 +352,15 @@ def run_fdas(args):
                  for name, code in FORMS.items() if name in args.forms}
 
     def step(s, ev=None):
+        """One fdas_search, through its two stages so that each can be timed."""
         p = s.p
         if ev is not None:
             ev[0].record(stream)
-        fdas.fdas_convolve(p, d_spec, args.n, s.tmpl, s.plane, s.ld, stream)
+        fdas.fdas_search_convolve(p, d_spec, args.n, s.tmpl, s.plane, s.ld, s.thresh, s.ws, s.ws_bytes, stream)
         if ev is not None:
             ev[1].record(stream)
-        fdas.fdas_harmonic_sum(p, s.plane, args.n, s.ld, s.thresh, s.cands, s.counts, s.peaks, s.ws, s.ws_bytes,
-                               stream)
+        fdas.fdas_search_harmonic(p, s.plane, args.n, s.ld, s.thresh, s.cands, s.counts, s.peaks, s.ws, s.ws_bytes,
+                                  stream)
         if ev is not None:
             ev[2].record(stream)
 
@@ -393,11 +415,11 @@ def run_fdas(args):
     cands, counts, _ = s.results(host=True)
 
     if rank == 0:
-        alg = algorithmic(args.n)
         hbm, hbm_kind = peaks()
         tc_peak, tc_kind = bf16_peak()
         forms = {}
         for name, r in results.items():
+            alg = algorithmic(args.n, rows_read=hs_rows(name))
             conv_s, hs_s = r["conv_ms"] / 1e3, r["hs_ms"] / 1e3
             conv_tflops = alg["conv_flop"] / conv_s / 1e12
             hs_gbs = alg["hs_bytes"] / hs_s / 1e9
@@ -418,7 +440,9 @@ def run_fdas(args):
                 "stages": {
                     "convolve": conv,
                     "harmonic_sum": {"ms": r["hs_ms"], "bound": "hbm", "achieved": hs_gbs, "unit": "GB/s",
-                                     "peak": hbm, "frac": hs_gbs / hbm, "traffic": traffic_for("harmonic.cu"),
+                                     "peak": hbm, "frac": hs_gbs / hbm,
+                                     "traffic": traffic_for("harmonic.cu" if name == "fp32" else "harmonic.cu+k1"),
+                                     "rows_read": hs_rows(name),
                                      "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({hbm_kind})"},
                 },
                 "clocks": samplers[name].summary(),
@@ -439,7 +463,7 @@ def run_fdas(args):
             "clocks": forms[head]["clocks"],
             "e2e": {"value": job_throughput(world, args.steps, e2e_s), "unit": "spectra/s",
                     "h2d_bytes_per_step": args.n * 8, "d2h_bytes_per_step": d2h},
-            "gpu_launches": (1 + hs_launches(p.n_harm, p.n_temp)) * args.steps,
+            "gpu_launches": search_launches(head, p.n_harm, p.n_temp) * args.steps,
             "roofline": roof,
             "stages": st,
             "forms": forms,

@@ -222,8 +222,10 @@ typedef struct {
 fdas_status fdas_convolve_cfg(const fdas_params *p, const void *d_spec, size_t n, const void *d_tmpl, float *d_plane,
                               size_t ld, const fdas_launch_config *cfg, fdas_stream_t stream);
 
-/* fdas_convolve followed by fdas_harmonic_sum on the same stream: the whole FDAS path for one
- * spectrum (Sec. 3.1, Eq. t_FDAS, with no separate FOP preparation). */
+/* The whole FDAS path for one spectrum (Sec. 3.1, Eq. t_FDAS, with no separate FOP preparation):
+ * fdas_search_convolve then fdas_search_harmonic on the same stream. The plane and the candidate
+ * lists equal those of fdas_convolve followed by fdas_harmonic_sum, bit for bit, except that when
+ * a plane has more than FDAS_RAW_CAP crossings the kept set (whichever arrived first) may differ. */
 fdas_status fdas_search(const fdas_params *p, const void *d_spec, size_t n, const void *d_tmpl,
                         float *d_plane, size_t ld, const float *d_thresh, fdas_cand *d_cands,
                         uint32_t *d_counts, fdas_cand *d_peaks, void *d_ws, size_t ws_bytes,
@@ -236,6 +238,21 @@ fdas_status fdas_search(const fdas_params *p, const void *d_spec, size_t n, cons
  * for the stream. d_cands, d_counts and d_peaks are device staging buffers of the same shapes as
  * in fdas_harmonic_sum (d_peaks may be NULL only if h_peaks is NULL).
  */
+/*
+ * The two stages of fdas_search, for callers that time or schedule them apart. Arguments as in
+ * fdas_search; both must run, in this order, on the same plane and workspace.
+ *   fdas_search_convolve: resets the workspace, then runs the convolution. With FDAS_FP32 it also
+ *     takes the HP_1 candidates and the HP_1 peak while each plane value is in registers: HP_1 is the
+ *     F-A plane itself (Algorithm 1 with k = 1), so the harmonic sum needs no single-plane pass.
+ *   fdas_search_harmonic: the remaining harmonic planes, detection and the candidate lists.
+ */
+fdas_status fdas_search_convolve(const fdas_params *p, const void *d_spec, size_t n, const void *d_tmpl,
+                                 float *d_plane, size_t ld, const float *d_thresh, void *d_ws, size_t ws_bytes,
+                                 fdas_stream_t stream);
+fdas_status fdas_search_harmonic(const fdas_params *p, const float *d_plane, size_t n, size_t ld,
+                                 const float *d_thresh, fdas_cand *d_cands, uint32_t *d_counts, fdas_cand *d_peaks,
+                                 void *d_ws, size_t ws_bytes, fdas_stream_t stream);
+
 fdas_status fdas_search_host(const fdas_params *p, const void *h_spec, size_t n, void *d_spec,
                              const void *d_tmpl, float *d_plane, size_t ld, const float *d_thresh,
                              fdas_cand *d_cands, uint32_t *d_counts, fdas_cand *d_peaks,

@@ -36,6 +36,8 @@ __all__ = [
     "fdas_harmonic_sum",
     "fdas_search",
     "fdas_search_host",
+    "fdas_search_convolve",
+    "fdas_search_harmonic",
     "fdas_harmonic_sum_noalloc",
     "decode_cands",
     "Searcher",
@@ -177,6 +179,25 @@ def fdas_search(p: Params, d_spec, n, d_tmpl, d_plane, ld, d_thresh, d_cands, d_
             _ptr(d_counts), _ptr(d_peaks), _ptr(d_ws), ws_bytes, _stream(stream),
         ),
         "fdas_search",
+    )
+
+
+def fdas_search_convolve(p: Params, d_spec, n, d_tmpl, d_plane, ld, d_thresh, d_ws, ws_bytes, stream=None):
+    """First stage of fdas_search: workspace reset, convolution (and HP_1 detection for FP32)."""
+    _check(
+        lib().fdas_search_convolve(C.byref(p.c()), _ptr(d_spec), n, _ptr(d_tmpl), _ptr(d_plane), ld, _ptr(d_thresh),
+                                   _ptr(d_ws), ws_bytes, _stream(stream)),
+        "fdas_search_convolve",
+    )
+
+
+def fdas_search_harmonic(p: Params, d_plane, n, ld, d_thresh, d_cands, d_counts, d_peaks, d_ws, ws_bytes,
+                         stream=None):
+    """Second stage of fdas_search: the remaining harmonic planes and the candidate lists."""
+    _check(
+        lib().fdas_search_harmonic(C.byref(p.c()), _ptr(d_plane), n, ld, _ptr(d_thresh), _ptr(d_cands),
+                                   _ptr(d_counts), _ptr(d_peaks), _ptr(d_ws), ws_bytes, _stream(stream)),
+        "fdas_search_harmonic",
     )
 
 

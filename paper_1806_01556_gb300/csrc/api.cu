@@ -174,6 +174,45 @@ fdas_status fdas_harmonic_sum(const fdas_params *p, const float *d_plane, size_t
         fdas::launch_harmonic(*p, d_plane, n, ld, d_thresh, d_cands, d_counts, d_peaks, ws, stream));
 }
 
+fdas_status fdas_search_convolve(const fdas_params *p, const void *d_spec, size_t n, const void *d_tmpl,
+                                 float *d_plane, size_t ld, const float *d_thresh, void *d_ws, size_t ws_bytes,
+                                 fdas_stream_t stream) {
+    fdas_status st = fdas_check_params(p);
+    if (st != FDAS_OK) return st;
+    if ((st = check_shape(p, n, ld)) != FDAS_OK) return st;
+    if (!d_spec || !d_tmpl || !d_plane || !d_thresh || !d_ws) return FDAS_ERR_INVALID_ARG;
+    if (!aligned16(d_spec) || !aligned16(d_tmpl) || !aligned16(d_plane) || !aligned16(d_ws)) return FDAS_ERR_INVALID_ARG;
+    if ((uintptr_t)d_thresh & 3u) return FDAS_ERR_INVALID_ARG;
+    if (ws_bytes < fdas_workspace_bytes(p, n)) return FDAS_ERR_WORKSPACE;
+    const Geometry g = fdas::geometry(*p);
+    const fdas::HsWorkspace ws = fdas::hs_workspace(d_ws, p->n_harm);
+    cudaError_t e = fdas::launch_hs_reset(*p, ws, stream);
+    if (e != cudaSuccess) return FDAS_ERR_CUDA;
+    const float2 *spec = static_cast<const float2 *>(d_spec);
+    const float2 *tmpl = static_cast<const float2 *>(d_tmpl);
+    if (g.precision == FDAS_FP32)
+        e = fdas::launch_convolve_hp1(g, spec, n, tmpl, d_plane, ld, d_thresh, p->harm_mask, p->n_harm, ws, stream);
+    else
+        e = fdas::launch_convolve(g, spec, n, tmpl, d_plane, ld, 0, 0, stream);
+    return cuda_status(e);
+}
+
+fdas_status fdas_search_harmonic(const fdas_params *p, const float *d_plane, size_t n, size_t ld,
+                                 const float *d_thresh, fdas_cand *d_cands, uint32_t *d_counts, fdas_cand *d_peaks,
+                                 void *d_ws, size_t ws_bytes, fdas_stream_t stream) {
+    fdas_status st = fdas_check_params(p);
+    if (st != FDAS_OK) return st;
+    if ((st = check_shape(p, n, ld)) != FDAS_OK) return st;
+    if (!d_plane || !d_thresh || !d_cands || !d_counts || !d_ws) return FDAS_ERR_INVALID_ARG;
+    if (!aligned16(d_plane) || !aligned16(d_ws) || ((uintptr_t)d_thresh & 3u) || ((uintptr_t)d_cands & 3u) ||
+        ((uintptr_t)d_counts & 3u) || ((uintptr_t)d_peaks & 3u))
+        return FDAS_ERR_INVALID_ARG;
+    if (ws_bytes < fdas_workspace_bytes(p, n)) return FDAS_ERR_WORKSPACE;
+    const fdas::HsWorkspace ws = fdas::hs_workspace(d_ws, p->n_harm);
+    return cuda_status(fdas::launch_harmonic(*p, d_plane, n, ld, d_thresh, d_cands, d_counts, d_peaks, ws, stream,
+                                             /*hp1_done=*/p->precision == FDAS_FP32));
+}
+
 fdas_status fdas_search(const fdas_params *p, const void *d_spec, size_t n, const void *d_tmpl, float *d_plane,
                         size_t ld, const float *d_thresh, fdas_cand *d_cands, uint32_t *d_counts, fdas_cand *d_peaks,
                         void *d_ws, size_t ws_bytes, fdas_stream_t stream) {
@@ -187,9 +226,9 @@ fdas_status fdas_search(const fdas_params *p, const void *d_spec, size_t n, cons
         ((uintptr_t)d_peaks & 3u))
         return FDAS_ERR_INVALID_ARG;
     if (ws_bytes < fdas_workspace_bytes(p, n)) return FDAS_ERR_WORKSPACE;
-    st = fdas_convolve(p, d_spec, n, d_tmpl, d_plane, ld, stream);
+    st = fdas_search_convolve(p, d_spec, n, d_tmpl, d_plane, ld, d_thresh, d_ws, ws_bytes, stream);
     if (st != FDAS_OK) return st;
-    return fdas_harmonic_sum(p, d_plane, n, ld, d_thresh, d_cands, d_counts, d_peaks, d_ws, ws_bytes, stream);
+    return fdas_search_harmonic(p, d_plane, n, ld, d_thresh, d_cands, d_counts, d_peaks, d_ws, ws_bytes, stream);
 }
 
 fdas_status fdas_search_host(const fdas_params *p, const void *h_spec, size_t n, void *d_spec, const void *d_tmpl,

@@ -38,8 +38,8 @@ fdas_status check_items(const fdas_params *p, const fdas_batch_item *items, int 
 struct Tables {
     ConvBatch conv;
     HsBatch hs;
-    int total_16k;  // harmonic-sum CTAs of all spectra in launches of 16384, 8192 and 4096 columns
-    int total_8k;
+    int total_16k;  // harmonic-sum CTAs of all spectra in launches of 16384, 12288 and 4096 columns
+    int total_12k;
     int total_4k;
 };
 
@@ -80,7 +80,7 @@ void build_tables(const fdas_params &p, const fdas_batch_item *items, int count,
     }
     t->conv.total_items = item;
     t->total_16k = blk2;
-    t->total_8k = blk;
+    t->total_12k = blk;
     t->total_4k = blk1;
 }
 
@@ -108,7 +108,7 @@ cudaError_t launch_batch(const fdas_params &p, const Tables &t, const void *d_tm
     cudaError_t e = fdas::launch_convolve_batch(g, t.conv, static_cast<const float2 *>(d_tmpl), grid,
                                                 cfg.templates_per_item, s);
     if (e != cudaSuccess || conv_only) return e;
-    return fdas::launch_harmonic_batch(p, t.hs, t.total_16k, t.total_8k, t.total_4k, d_thresh, s);
+    return fdas::launch_harmonic_batch(p, t.hs, t.total_16k, t.total_12k, t.total_4k, d_thresh, s);
 }
 
 }  // namespace

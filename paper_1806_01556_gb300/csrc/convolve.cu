@@ -19,6 +19,7 @@
 // stores from one base pointer per template.
 #include <utility>
 
+#include "hs_keys.cuh"
 #include "ols_common.cuh"
 
 namespace fdas {
@@ -27,9 +28,48 @@ namespace {
 // Two exchange buffers, two template buffers, and two mbarriers for the template copies.
 constexpr size_t kSmemBytes = (2 * kPadded + 2 * kF) * sizeof(float2) + 2 * sizeof(unsigned long long);
 
-template <class Jobs>
+// HP_1 detection fused into the convolution (fdas_search): HP_1(i, j) is the plane value itself
+// (Algorithm 1 with k = 1), so for the rows that take part in no other plane (|i| > c/2) the
+// candidates above TA(1, i) and the HP_1 peak are taken while the values are in registers, and the
+// harmonic sum skips its single-plane launch. The row-group launches still take HP_1 of their rows.
+struct Hp1 {
+    const float *ta;  // TA(1, row) for every row; nullptr: no HP_1 candidates (bit 0 of harm_mask clear)
+    unsigned long long *raw;
+    unsigned long long *counters;
+    unsigned long long *peaks;
+    int c;            // zero-drift row
+    int lo1;          // rows with |row - c| >= lo1 are the single-plane rows this kernel takes
+};
+
+// Rare path, kept out of line so that the hot loop stays small: emit the kept outputs of one row
+// segment above ta, re-read from the plane (the calling warp must be converged: emit ballots).
+__device__ __noinline__ void hp1_emit_row(const float *rowp, float ta, int t, int col, unsigned smask, Hp1 hp1) {
+#pragma unroll 1
+    for (int q = 0; q < 16; ++q) {
+        const int o = 128 * (q >> 3) + 256 * (q & 7);
+        const bool kept = (smask >> q) & 1u;
+        const float pv = kept ? rowp[o] : -1.0f;
+        emit(kept && pv > ta, pv, t, (unsigned)(col + o), 1, threadIdx.x & 31, hp1.counters, hp1.raw);
+    }
+}
+
+// Column (as row << 24 | column) of the first kept output equal to best in one row segment.
+__device__ __noinline__ unsigned hp1_best_loc(const float *rowp, float best, int t, int col, unsigned smask) {
+    unsigned loc = 0xFFFFFFFFu;
+#pragma unroll 1
+    for (int q = 0; q < 16; ++q) {
+        const int o = 128 * (q >> 3) + 256 * (q & 7);
+        if (((smask >> q) & 1u) && rowp[o] == best) {
+            const unsigned l = ((unsigned)t << 24) | (unsigned)(col + o);
+            loc = l < loc ? l : loc;
+        }
+    }
+    return loc;
+}
+
+template <bool HP1, class Jobs>
 __global__ void __launch_bounds__(kThreads, 3)
-    fdas_ols_fp32(Jobs jobs, const float2 *__restrict__ tmpl, int n_temp, int h, int keep) {
+    fdas_ols_fp32(Jobs jobs, const float2 *__restrict__ tmpl, int n_temp, int h, int keep, Hp1 hp1) {
     extern __shared__ __align__(128) float2 smem[];
     float2 *buf0 = smem;
     float2 *buf1 = smem + kPadded;
@@ -97,6 +137,8 @@ __global__ void __launch_bounds__(kThreads, 3)
             v[r] = (idx >= 0 && idx < n) ? __ldg(&spec[idx]) : make_float2(0.f, 0.f);
         }
         fft_passes_12<false>(v, buf0, buf1, tw2, tid, [] {});
+        float best = -1.0f;  // HP1: this thread's largest single-plane-row output of the item, its template
+        int best_t = -1;
         float2 W[16];
         {
             float2 u[8];
@@ -125,6 +167,8 @@ __global__ void __launch_bounds__(kThreads, 3)
             // Column col0 + b + 256 r of row t, for b = tid + 128 hh: one base pointer per half, then
             // constant offsets; a plain predicated store per output.
             float *const dst = it.plane + (size_t)t * it.ld + col0 + tid;
+            const bool k1row = HP1 && abs(t - hp1.c) >= hp1.lo1;  // CTA-uniform
+            float mx = -1.0f;  // HP1: largest kept output of this template
 #pragma unroll
             for (int hh = 0; hh < 2; ++hh) {
                 float2 u[8];
@@ -133,9 +177,29 @@ __global__ void __launch_bounds__(kThreads, 3)
 #pragma unroll
                 for (int r = 0; r < 8; ++r) {
                     const float pw = fmaf(u[r].x, u[r].x, u[r].y * u[r].y);
-                    if ((m8 >> r) & 1u) dst[128 * hh + 256 * r] = pw;
+                    if ((m8 >> r) & 1u) {
+                        dst[128 * hh + 256 * r] = pw;
+                        if (k1row) mx = fmaxf(mx, pw);
+                    }
                 }
             }
+            if (k1row) {
+                const float ta = hp1.ta ? __ldg(&hp1.ta[t]) : __int_as_float(0x7f800000);
+                if (__any_sync(0xFFFFFFFFu, mx > ta)) hp1_emit_row(dst, ta, t, col0 + tid, smask, hp1);  // rare
+                if (mx > best) {  // strict: the first template wins ties, as in the canonical order
+                    best = mx;
+                    best_t = t;
+                }
+            }
+        }
+        if (HP1) {
+            // The HP_1 peak of the item's single-plane rows: the column of this thread's best
+            // (re-read from its row), then the warp's largest key, one atomicMax per warp.
+            const unsigned loc = best_t >= 0 ? hp1_best_loc(it.plane + (size_t)best_t * it.ld + col0 + tid, best,
+                                                            best_t, col0 + tid, smask)
+                                             : 0xFFFFFFFFu;
+            const unsigned long long key = warp_peak_key_loc(best, loc);
+            if ((tid & 31) == 0 && key != 0ull) atomicMax(&hp1.peaks[0], key);
         }
     }
 }
@@ -173,9 +237,10 @@ cudaError_t launch_convolve_fp32(const Geometry &g, const float2 *spec, size_t n
     int grid = 0;
     cudaError_t e = persistent_grid(jobs.n_seg * jobs.n_tchunk, ctas_per_sm, &grid);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(fdas_ols_fp32<SingleJobs>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    e = cudaFuncSetAttribute(fdas_ols_fp32<false, SingleJobs>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kSmemBytes);
     if (e != cudaSuccess) return e;
-    fdas_ols_fp32<<<grid, kThreads, kSmemBytes, s>>>(jobs, tmpl, g.n_temp, g.h, g.keep);
+    fdas_ols_fp32<false><<<grid, kThreads, kSmemBytes, s>>>(jobs, tmpl, g.n_temp, g.h, g.keep, Hp1{});
     return cudaGetLastError();
 }
 
@@ -207,6 +272,27 @@ cudaError_t check_wait_timeout(unsigned *flags) {
     return e;
 }
 
+cudaError_t launch_convolve_hp1(const Geometry &g, const float2 *spec, size_t n, const float2 *tmpl, float *plane,
+                                size_t ld, const float *thresh, unsigned harm_mask, int n_harm, const HsWorkspace &ws,
+                                cudaStream_t s) {
+    SingleJobs jobs;
+    jobs.spec = spec;
+    jobs.plane = plane;
+    jobs.ld = ld;
+    jobs.n = (int)n;
+    jobs.n_seg = (int)((n + g.keep - 1) / g.keep);
+    jobs.n_temp = g.n_temp;
+    chunking(g, 0, &jobs.t_chunk, &jobs.n_tchunk);
+    cudaError_t e = cudaFuncSetAttribute(fdas_ols_fp32<true, SingleJobs>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kSmemBytes);
+    if (e != cudaSuccess) return e;
+    // The single-plane rows: |i| > c/2 with two or more planes, every row with one.
+    const Hp1 hp1{(harm_mask & 1u) ? thresh : nullptr, ws.raw, ws.counters, ws.peaks, g.c, n_harm >= 2 ? g.c / 2 + 1 : 0};
+    fdas_ols_fp32<true><<<jobs.n_seg * jobs.n_tchunk, kThreads, kSmemBytes, s>>>(jobs, tmpl, g.n_temp, g.h, g.keep,
+                                                                                hp1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_convolve(const Geometry &g, const float2 *spec, size_t n, const float2 *tmpl, float *plane,
                             size_t ld, int ctas_per_sm, int templates_per_item, cudaStream_t s) {
     if (g.precision == FDAS_FP32)
@@ -227,8 +313,8 @@ cudaError_t device_status(unsigned *flags, bool clear) {
 }
 
 cudaError_t prepare_convolve_batch() {
-    cudaError_t e = cudaFuncSetAttribute(fdas_ols_fp32<BatchJobs>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kSmemBytes);
+    cudaError_t e = cudaFuncSetAttribute(fdas_ols_fp32<false, BatchJobs>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
     if (e == cudaSuccess) e = prepare_convolve_batch_tc();
     return e;
 }
@@ -246,7 +332,7 @@ cudaError_t launch_convolve_batch(const Geometry &g, const ConvBatch &batch, con
     jobs.batch = batch;
     jobs.n_temp = g.n_temp;
     chunking(g, templates_per_item, &jobs.t_chunk, &jobs.n_tchunk);
-    fdas_ols_fp32<<<grid, kThreads, kSmemBytes, s>>>(jobs, tmpl, g.n_temp, g.h, g.keep);
+    fdas_ols_fp32<false><<<grid, kThreads, kSmemBytes, s>>>(jobs, tmpl, g.n_temp, g.h, g.keep, Hp1{});
     return cudaGetLastError();
 }
 

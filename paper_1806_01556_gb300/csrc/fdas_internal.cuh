@@ -71,7 +71,7 @@ struct HsJob {
     const float *plane;
     unsigned long long ld;
     int n;
-    int blk0;   // first CTA of this spectrum in harmonic-sum launches of 8192-column CTAs
+    int blk0;   // first CTA of this spectrum in harmonic-sum launches of 12288-column CTAs
     int blk1;   // first CTA of this spectrum in harmonic-sum launches of 4096-column CTAs
     int blk2;   // first CTA of this spectrum in harmonic-sum launches of 16384-column CTAs
     unsigned long long *counters;  // this spectrum's workspace (HsWorkspace)
@@ -104,6 +104,14 @@ cudaError_t launch_convolve_batch_tc(const Geometry &g, const ConvBatch &batch, 
 cudaError_t device_status_tc(unsigned *flags, bool clear);
 // Resident CTAs per SM of the convolution kernel for g.precision.
 inline int convolve_ctas_per_sm(const Geometry &g) { return g.precision == FDAS_FP32 ? 3 : kTcMaxCtasPerSm; }
+// Zeroes the harmonic-sum workspace's counters and peak keys.
+cudaError_t launch_hs_reset(const fdas_params &p, const HsWorkspace &ws, cudaStream_t s);
+// FP32 convolution that also emits, for the single-plane rows (|i| > c/2; all rows when n_harm = 1),
+// the HP_1 candidates (threshold thresh[0..n_temp), when bit 0 of harm_mask is set) and their HP_1
+// peak into the workspace, which must have been reset.
+cudaError_t launch_convolve_hp1(const Geometry &g, const float2 *spec, size_t n, const float2 *tmpl, float *plane,
+                                size_t ld, const float *thresh, unsigned harm_mask, int n_harm, const HsWorkspace &ws,
+                                cudaStream_t s);
 // Status bits set by kernels on the device (bit 0: a bounded wait timed out); optionally cleared.
 cudaError_t device_status(unsigned *flags, bool clear);
 // Runs a kernel whose bounded wait must give up; returns the status bits it left (then cleared).
@@ -113,13 +121,15 @@ cudaError_t prepare_convolve_batch();
 int convolve_items(const Geometry &g, size_t n, int templates_per_item);
 cudaError_t launch_convolve_batch(const Geometry &g, const ConvBatch &batch, const float2 *tmpl, int grid,
                                   int templates_per_item, cudaStream_t s);
+// Harmonic sum. With hp1_done the workspace was reset before the convolution, which already took
+// HP_1 of the single-plane rows (launch_convolve_hp1).
 cudaError_t launch_harmonic(const fdas_params &p, const float *plane, size_t n, size_t ld,
                             const float *thresh, fdas_cand *cands, uint32_t *counts, fdas_cand *peaks,
-                            const HsWorkspace &ws, cudaStream_t s);
+                            const HsWorkspace &ws, cudaStream_t s, bool hp1_done = false);
 // Batched harmonic sum: reset, one launch per group of rows over every spectrum, finalize.
-void harmonic_blocks(const fdas_params &p, size_t n, int *blocks_16k, int *blocks_8k, int *blocks_4k);
+void harmonic_blocks(const fdas_params &p, size_t n, int *blocks_16k, int *blocks_12k, int *blocks_4k);
 cudaError_t prepare_harmonic_batch();
-cudaError_t launch_harmonic_batch(const fdas_params &p, const HsBatch &batch, int total_16k, int total_8k,
+cudaError_t launch_harmonic_batch(const fdas_params &p, const HsBatch &batch, int total_16k, int total_12k,
                                   int total_4k, const float *thresh, cudaStream_t s);
 
 }  // namespace fdas

@@ -23,24 +23,13 @@
 //                    shared memory, and at most one 64-bit atomicMax per block and plane.
 //   fdas_hs_finalize one CTA per plane. It bitonic-sorts the raw keys in shared memory, then decodes
 //                    the top cand_cap keys into fdas_cand records and writes the counts and peaks.
-#include "fdas_internal.cuh"
+#include "hs_keys.cuh"
 
 namespace fdas {
 namespace {
 
 constexpr int kHsThreads = 256;
 constexpr int kFinThreads = 1024;
-
-// Candidate key, ascending = canonical order (power desc, then row i asc, then column j asc).
-__device__ __forceinline__ unsigned long long cand_key(float power, int row, unsigned j) {
-    const unsigned pb = __float_as_uint(power);  // power >= 0, so the bits order like the values
-    return ((unsigned long long)(0xFFFFFFFFu - pb) << 32) | ((unsigned long long)row << 24) | j;
-}
-// Peak key, descending = canonical order.
-__device__ __forceinline__ unsigned long long peak_key(float power, int row, unsigned j) {
-    const unsigned pb = __float_as_uint(power);
-    return ((unsigned long long)pb << 32) | (0xFFFFFFFFu - (((unsigned)row << 24) | j));
-}
 
 __global__ void fdas_hs_reset(unsigned long long *counters, unsigned long long *peaks, int n_harm) {
     const int t = threadIdx.x;
@@ -51,31 +40,6 @@ __global__ void fdas_hs_reset(unsigned long long *counters, unsigned long long *
 }
 
 constexpr int kHsWarps = kHsThreads / 32;
-
-// Warp-wide candidate compaction: one ballot, one atomicAdd per warp, a prefix popcount per lane.
-__device__ __forceinline__ void emit(bool hit, float hp, int row, unsigned j, int plane_k, int lane,
-                                     unsigned long long *counters, unsigned long long *raw) {
-    const unsigned ballot = __ballot_sync(0xFFFFFFFFu, hit);
-    if (!ballot) return;
-    const int leader = __ffs(ballot) - 1;
-    unsigned long long base = 0;
-    if (lane == leader) base = atomicAdd(&counters[plane_k - 1], (unsigned long long)__popc(ballot));
-    base = __shfl_sync(0xFFFFFFFFu, base, leader);
-    if (hit) {
-        const unsigned long long slot = base + __popc(ballot & ((1u << lane) - 1u));
-        if (slot < FDAS_RAW_CAP) raw[(size_t)(plane_k - 1) * FDAS_RAW_CAP + slot] = cand_key(hp, row, j);
-    }
-}
-
-// The loudest point of plane k over a warp: redux max of the power bits (non-negative floats order
-// like their bits), then redux min of the column among the lanes that hold that power.
-__device__ __forceinline__ unsigned long long warp_peak_key(float best, int bestj, int row) {
-    const unsigned pb = best >= 0.0f ? __float_as_uint(best) : 0u;
-    const unsigned mx = __reduce_max_sync(0xFFFFFFFFu, pb);
-    const unsigned jmin = __reduce_min_sync(0xFFFFFFFFu, (best >= 0.0f && pb == mx) ? (unsigned)bestj : 0xFFFFFFFFu);
-    if (jmin == 0xFFFFFFFFu) return 0ull;
-    return peak_key(__uint_as_float(mx), row, jmin);
-}
 
 // Block-level merge of the warps' peak keys and one atomicMax per block and plane, skipped when the
 // block's key cannot win (peak keys only grow).
@@ -156,10 +120,11 @@ __device__ __forceinline__ int term_count(int j, int n) {
 // boundary j = (n-1)/l.
 constexpr int kChunks = 8;
 // Fundamentals per thread and chunk: more for few planes (more gathers in flight per thread: the
-// 2- and 4-plane launches went from 0.166 to 0.126 ms at N = 2^21 with 8 instead of 4), fewer for
-// many planes, to keep the gathers in registers.
+// 2- and 4-plane launches went from 0.166 to 0.126 ms at N = 2^21 with 8 instead of 4, the 5- to
+// 8-plane launch gained 4% with 6 instead of 4), fewer for many planes, to keep the gathers in
+// registers (8 for up to 8 planes spilled and lost 10%).
 template <int KL>
-__host__ __device__ constexpr int jpt() { return KL <= 4 ? 8 : KL <= 9 ? 4 : 2; }
+__host__ __device__ constexpr int jpt() { return KL <= 4 ? 8 : KL <= 9 ? 6 : 2; }
 
 template <int KL, bool UNIFORM>
 __device__ __forceinline__ void hs_chunk(const float *const (&rp)[KL], const float (&ta)[KL], int n, int row,
@@ -463,10 +428,10 @@ __global__ void __launch_bounds__(kFinThreads)
 // ---- batched forms: one launch per stage for every spectrum of a batch ----------------------------
 
 // Spectrum of CTA x in a launch of W columns per CTA: the last job whose first CTA in such launches
-// (blk2 for 16384 columns, blk0 for 8192, blk1 for 4096) is <= x.
+// (blk2 for 16384 columns, blk0 for 12288, blk1 for 4096) is <= x.
 template <int W>
 __device__ __forceinline__ int first_block(const HsJob &J) {
-    return W == 16384 ? J.blk2 : W == 8192 ? J.blk0 : J.blk1;
+    return W == 16384 ? J.blk2 : W == 12288 ? J.blk0 : J.blk1;
 }
 template <int W>
 __device__ __forceinline__ int job_of_block(const HsBatch &B, int x) {
@@ -499,7 +464,7 @@ __global__ void __launch_bounds__(kHsThreads, 4)
               vec);
 }
 
-// CTA widths: 16384 columns (kernels for up to 4 terms), 8192 (up to 8) or 4096 (16 terms, and the
+// CTA widths: 16384 columns (kernels for up to 4 terms), 12288 (up to 8) or 4096 (16 terms, and the
 // single-plane rows). HsJob.blk2 / blk0 / blk1 are the spectrum's first CTA in launches of each width.
 template <int KL>
 __global__ void __launch_bounds__(kHsThreads, KL <= 3 ? 4 : 2)
@@ -534,12 +499,22 @@ HsBatchKernel hs_batch_kernel(int kmax) {
 
 }  // namespace
 
+cudaError_t launch_hs_reset(const fdas_params &p, const HsWorkspace &ws, cudaStream_t s) {
+    fdas_hs_reset<<<1, 32, 0, s>>>(ws.counters, ws.peaks, p.n_harm);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_harmonic(const fdas_params &p, const float *plane, size_t n, size_t ld, const float *thresh,
                             fdas_cand *cands, uint32_t *counts, fdas_cand *peaks, const HsWorkspace &ws,
-                            cudaStream_t s) {
-    fdas_hs_reset<<<1, 32, 0, s>>>(ws.counters, ws.peaks, p.n_harm);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+                            cudaStream_t s, bool hp1_done) {
+    // hp1_done: the workspace was reset before the convolution, which also took the HP_1 candidates
+    // and peak of the single-plane rows; no single-plane launch runs then.
+    cudaError_t e = cudaSuccess;
+    if (!hp1_done) {
+        e = launch_hs_reset(p, ws, s);
+        if (e != cudaSuccess) return e;
+    }
+    const unsigned mask = p.harm_mask;
     // Rows with at least two planes in a few launches (kGroups), then the single-plane rows
     // (|i| > c/2; every row when n_harm = 1) streamed by fdas_hs_k1.
     const int c = (p.n_temp - 1) / 2;
@@ -551,12 +526,12 @@ cudaError_t launch_harmonic(const fdas_params &p, const float *plane, size_t n, 
         const int per = kChunks * kHsThreads * kl_width(kmax);
         const int rows = (lo == 0) ? 2 * hi + 1 : 2 * (hi - lo + 1);
         hs_kernel(kmax)<<<dim3((unsigned)((n + per - 1) / per), (unsigned)rows), kHsThreads, 0, s>>>(
-            plane, (int)n, ld, thresh, p.n_temp, p.harm_mask, p.n_harm, lo, ws.raw, ws.counters, ws.peaks);
+            plane, (int)n, ld, thresh, p.n_temp, mask, p.n_harm, lo, ws.raw, ws.counters, ws.peaks);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     const int rows1 = lo1 == 0 ? 2 * c + 1 : 2 * (c - lo1 + 1);
-    if (rows1 > 0) {
+    if (rows1 > 0 && !hp1_done) {
         fdas_hs_k1<<<dim3((unsigned)((n + kK1Cols - 1) / kK1Cols), (unsigned)rows1), kHsThreads, 0, s>>>(
             plane, (int)n, ld, thresh, p.n_temp, p.harm_mask, lo1, ws.raw, ws.counters, ws.peaks);
         e = cudaGetLastError();
@@ -570,16 +545,16 @@ cudaError_t launch_harmonic(const fdas_params &p, const float *plane, size_t n, 
     return cudaGetLastError();
 }
 
-// CTAs of one spectrum of n bins in launches of 16384, 8192 and 4096 columns per CTA (rows with up to
-// 4, up to 8 and 16 planes; the single-plane rows use 4096 too).
-void harmonic_blocks(const fdas_params &p, size_t n, int *blocks_16k, int *blocks_8k, int *blocks_4k) {
+// CTAs of one spectrum of n bins in launches of 16384, 12288 and 4096 columns per CTA (rows with up
+// to 4, up to 8 and 16 planes; the single-plane rows use 4096 too).
+void harmonic_blocks(const fdas_params &p, size_t n, int *blocks_16k, int *blocks_12k, int *blocks_4k) {
     (void)p;
     static_assert(kChunks * kHsThreads * jpt<2>() == 16384 && kChunks * kHsThreads * jpt<4>() == 16384,
                   "rows with up to 4 planes: 16384 columns per CTA");
-    static_assert(kChunks * kHsThreads * jpt<8>() == 8192, "rows with up to 8 planes: 8192 columns per CTA");
+    static_assert(kChunks * kHsThreads * jpt<8>() == 12288, "rows with up to 8 planes: 12288 columns per CTA");
     static_assert(kChunks * kHsThreads * jpt<16>() == kK1Cols, "16 planes and single-plane rows: 4096 columns");
     *blocks_16k = (int)((n + 16383) / 16384);
-    *blocks_8k = (int)((n + 8191) / 8192);
+    *blocks_12k = (int)((n + 12287) / 12288);
     *blocks_4k = (int)((n + kK1Cols - 1) / kK1Cols);
 }
 
@@ -588,7 +563,7 @@ cudaError_t prepare_harmonic_batch() {
                                 FDAS_RAW_CAP * (int)sizeof(unsigned long long));
 }
 
-cudaError_t launch_harmonic_batch(const fdas_params &p, const HsBatch &B, int total_16k, int total_8k, int total_4k,
+cudaError_t launch_harmonic_batch(const fdas_params &p, const HsBatch &B, int total_16k, int total_12k, int total_4k,
                                   const float *thresh, cudaStream_t s) {
     fdas_hs_reset_batch<<<B.count, 32, 0, s>>>(B, p.n_harm);
     cudaError_t e = cudaGetLastError();
@@ -601,7 +576,7 @@ cudaError_t launch_harmonic_batch(const fdas_params &p, const HsBatch &B, int to
         const int kmax = gr.kmax < p.n_harm ? gr.kmax : p.n_harm;
         const int rows = (lo == 0) ? 2 * hi + 1 : 2 * (hi - lo + 1);
         const int w = kChunks * kHsThreads * kl_width(kmax);
-        const unsigned gx = (unsigned)(w == 16384 ? total_16k : w == 8192 ? total_8k : total_4k);
+        const unsigned gx = (unsigned)(w == 16384 ? total_16k : w == 12288 ? total_12k : total_4k);
         hs_batch_kernel(kmax)<<<dim3(gx, (unsigned)rows), kHsThreads, 0, s>>>(B, thresh, p.n_temp, p.harm_mask,
                                                                              p.n_harm, lo);
         e = cudaGetLastError();

@@ -141,6 +141,8 @@ def test_python_wrappers_marshal_and_raise_on_rejected_arguments(fd):
     st = _NullStream()
     calls = [
         lambda: fd.fdas_convolve(p, buf, 0, buf, buf, 0, st),
+        lambda: fd.fdas_search_convolve(p, buf, 0, buf, buf, 0, buf, buf, 1 << 20, st),
+        lambda: fd.fdas_search_harmonic(p, buf, 0, 0, buf, buf, buf, buf, buf, 1 << 20, st),
         lambda: fd.fdas_convolve_cfg(p, buf, 0, buf, buf, 0, 2, 17, st),
         lambda: fd.fdas_harmonic_sum(p, buf, 0, 0, buf, buf, buf, None, buf, 1 << 30, st),
         lambda: fd.fdas_search(p, buf, 0, buf, buf, 0, buf, buf, buf, None, buf, 1 << 30, st),

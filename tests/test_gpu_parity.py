@@ -322,3 +322,61 @@ def test_bounded_wait_gives_up_and_the_context_stays_usable(fd, small_case):
     mx, _ = plane_rel(got, ref)
     assert mx <= REL_TOL
     assert fd.fdas_device_status() == 0
+
+
+def _search_both_ways(fd, p, spec, thresh, ld=None):
+    """fdas_search (HP_1 taken by the convolution) and fdas_convolve + fdas_harmonic_sum."""
+    n = len(spec)
+    ld = n if ld is None else ld
+    tmpl = torch.empty(fd.fdas_templates_bytes(p), dtype=torch.uint8, device="cuda")
+    fd.fdas_make_templates(p, tmpl)
+    d_spec = torch.from_numpy(np.ascontiguousarray(spec, dtype=np.complex64)).cuda()
+    d_ta = torch.from_numpy(np.ascontiguousarray(thresh, dtype=np.float32)).cuda()
+    ws_bytes = fd.fdas_workspace_bytes(p, n)
+    out = []
+    for fused in (True, False):
+        plane = torch.full((p.n_temp, ld), np.nan, dtype=torch.float32, device="cuda")
+        ws = torch.full((ws_bytes,), 0xCD, dtype=torch.uint8, device="cuda")
+        cands = torch.zeros(p.n_harm * p.cand_cap * 12, dtype=torch.uint8, device="cuda")
+        counts = torch.zeros(p.n_harm, dtype=torch.int32, device="cuda")
+        peaks = torch.zeros(p.n_harm * 12, dtype=torch.uint8, device="cuda")
+        if fused:
+            fd.fdas_search(p, d_spec, n, tmpl, plane, ld, d_ta, cands, counts, peaks, ws, ws_bytes)
+        else:
+            fd.fdas_convolve(p, d_spec, n, tmpl, plane, ld)
+            fd.fdas_harmonic_sum(p, plane, n, ld, d_ta, cands, counts, peaks, ws, ws_bytes)
+        torch.cuda.synchronize()
+        cnt = counts.cpu().numpy().astype(np.uint32)
+        out.append((plane.cpu().numpy(), fd.decode_cands(cands.cpu().numpy(), cnt, p.cand_cap), cnt,
+                    peaks.cpu().numpy().view(fd.CAND_DTYPE)))
+    return out
+
+
+@pytest.mark.parametrize(
+    "n,kw,sigma",
+    [
+        (1, {}, 6.0),
+        (211, {}, 3.0),
+        (5000, {}, 3.0),
+        (40000, dict(cand_cap=1000), 3.5),
+        (40000, dict(harm_mask=0b11111110), 3.5),
+        (40000, dict(n_harm=1, harm_mask=1, cand_cap=1000), 3.5),
+        (40000, dict(n_harm=16, harm_mask=0xFFFF), 3.5),
+        (30000, dict(n_temp=9, z_min=-8, z_step=2, n_tap=129, n_harm=4, harm_mask=0xF), 3.0),
+    ],
+)
+def test_search_with_fused_hp1_equals_separate_calls(fd, n, kw, sigma):
+    """fdas_search takes HP_1 inside the convolution; its plane, candidates, counts and peaks equal
+    those of fdas_convolve followed by fdas_harmonic_sum, bit for bit (below FDAS_RAW_CAP)."""
+    p = fd.Params(**kw)
+    wl = synth.small_workload(n=max(n, 64))
+    spec = wl.spectrum[:n].copy()
+    ta = thresholds.threshold_array(p.n_harm, p.n_temp, sigma=sigma)
+    (pa, ca, na, ka), (pb, cb, nb, kb) = _search_both_ways(fd, p, spec, ta, ld=n + 3 * (n % 2 == 0))
+    assert np.array_equal(pa.view(np.uint32)[:, :n], pb.view(np.uint32)[:, :n])
+    assert np.array_equal(na, nb) and int(na.max()) < 16384
+    for k in range(p.n_harm):
+        assert np.array_equal(ca[k], cb[k]), k
+    assert np.array_equal(ka, kb)
+    if p.harm_mask & 1:
+        assert int(na[0]) > 0 or n < 64
