@@ -106,10 +106,12 @@ def hs_launches(n_harm=8, n_temp=85):
     return 2 + groups + k1
 
 
-def search_launches(precision, n_harm=8, n_temp=85):
+def search_launches(precision, n_harm=8, n_temp=85, harm_index=0):
     """Kernel launches of one fdas_search (its two stages). FP32 takes HP_1 in the convolution, so
     its launches are reset, convolution, the row groups and finalize: as many as a harmonic sum
     alone. The tensor-core forms: reset, convolution, then the whole harmonic sum."""
+    if harm_index:
+        return 5  # reset, convolution, reset, the highest-harmonic launch, finalize
     return hs_launches(n_harm, n_temp) + (0 if precision == "fp32" else 2)
 
 
@@ -312,12 +314,12 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def workload_config(n):
+def workload_config(n, n_tap=421):
     return {
         "workload": f"SKA-sized spectrum N={n} (2^{int(np.log2(n))}), 4 drifting tones x 8 harmonics in unit "
-                    "complex Gaussian noise (seed 1, rank r uses seed 1+r); 85 templates z=-42..42, 421 taps, "
+                    f"complex Gaussian noise (seed 1, rank r uses seed 1+r); 85 templates z=-42..42, {n_tap} taps, "
                     "overlap-save F=2048; 8 harmonic planes, 6-sigma thresholds, 200 candidates per plane",
-        "n": n, "n_temp": 85, "n_tap": 421, "fft_len": 2048, "n_harm": 8,
+        "n": n, "n_temp": 85, "n_tap": n_tap, "fft_len": 2048, "n_harm": 8,
         "l2": "inputs larger than L2: the 713 MB plane is written and read every step",
         "parallelism": "replicas (one spectrum per GPU, no collective)",
     }
@@ -348,7 +350,8 @@ def run_fdas(args):
 
     d_spec = torch.from_numpy(wl.spectrum).to(dev)
     stream = torch.cuda.current_stream(dev)
-    searchers = {name: fdas.Searcher(fdas.Params(precision=code), args.n, device=f"cuda:{local}")
+    searchers = {name: fdas.Searcher(fdas.Params(precision=code, n_tap=args.n_tap, harm_index=args.harm_index),
+                                     args.n, device=f"cuda:{local}")
                  for name, code in FORMS.items() if name in args.forms}
 
     def step(s, ev=None):
@@ -419,7 +422,7 @@ def run_fdas(args):
         tc_peak, tc_kind = bf16_peak()
         forms = {}
         for name, r in results.items():
-            alg = algorithmic(args.n, rows_read=hs_rows(name))
+            alg = algorithmic(args.n, n_tap=args.n_tap, rows_read=85 if args.harm_index else hs_rows(name))
             conv_s, hs_s = r["conv_ms"] / 1e3, r["hs_ms"] / 1e3
             conv_tflops = alg["conv_flop"] / conv_s / 1e12
             hs_gbs = alg["hs_bytes"] / hs_s / 1e9
@@ -429,7 +432,7 @@ def run_fdas(args):
                     "hbm_gbs": alg["conv_bytes"] / conv_s / 1e9,
                     "traffic": traffic_for("convolve.cu" if name == "fp32" else "convolve_tc.cu")}
             if name != "fp32":
-                executed = tc_executed_flop(args.n)
+                executed = tc_executed_flop(args.n, n_tap=args.n_tap)
                 conv["tensor"] = {"executed_tflops": executed / conv_s / 1e12, "peak": tc_peak,
                                   "frac": executed / conv_s / 1e12 / tc_peak,
                                   "peak_source": f"MEASURED_PEAKS.json bf16_tflops ({tc_kind})",
@@ -453,7 +456,8 @@ def run_fdas(args):
         roof = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
                 "frac": d["frac"], "traffic": d["traffic"], "peak_source": d["peak_source"]}
         d2h = p.n_harm * p.cand_cap * 12 + p.n_harm * 4 + p.n_harm * 12
-        cfg = workload_config(args.n)
+        cfg = workload_config(args.n, args.n_tap)
+        cfg["harm_index"] = "highest" if args.harm_index else "fundamental"
         cfg["precision"] = head
         line = {
             "metric": METRIC, "value": value, "unit": "spectra/s", "n_gpus": world, "steps": args.steps,
@@ -463,7 +467,7 @@ def run_fdas(args):
             "clocks": forms[head]["clocks"],
             "e2e": {"value": job_throughput(world, args.steps, e2e_s), "unit": "spectra/s",
                     "h2d_bytes_per_step": args.n * 8, "d2h_bytes_per_step": d2h},
-            "gpu_launches": search_launches(head, p.n_harm, p.n_temp) * args.steps,
+            "gpu_launches": search_launches(head, p.n_harm, p.n_temp, args.harm_index) * args.steps,
             "roofline": roof,
             "stages": st,
             "forms": forms,
@@ -609,7 +613,7 @@ def run_profile(args):
     wl = synth.ska_workload(n=args.n, seed=1)
     d_spec = torch.from_numpy(wl.spectrum).cuda()
     for name in args.forms:
-        s = fdas.Searcher(fdas.Params(precision=FORMS[name]), args.n)
+        s = fdas.Searcher(fdas.Params(precision=FORMS[name], n_tap=args.n_tap), args.n)
         for _ in range(args.steps):
             s.search(d_spec, args.n)
         torch.cuda.synchronize()
@@ -624,6 +628,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="fdas", choices=["fdas", "reference"])
     ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--harm-index", type=int, default=0, choices=[0, 1],
+                    help="harmonic-plane indexing: 0 by fundamental (default), 1 by highest harmonic")
+    ap.add_argument("--n-tap", type=int, default=421, help="taps per template (odd; the paper's reduced variants "
+                    "256 and 128 are run as 257 and 129)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="single", choices=["single", "batch", "serve", "profile"])
     ap.add_argument("--rate", type=float, default=200.0)

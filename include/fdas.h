@@ -67,8 +67,18 @@ typedef int fdas_status;
  *   n_harm    N_hp, harmonic planes summed, 1..16. Default 8.
  *   harm_mask bit k-1 set: report candidates of HP_k. Nonzero, no bit at or above n_harm.
  *   cand_cap  N_cand, candidates kept per reported plane, 1..4096. Default 200.
- *   precision FDAS_FP32.
+ *   precision  arithmetic of the FT convolution: FDAS_FP32 (default), FDAS_BF16X3 or FDAS_FP16S
+ *              (the inverse DFTs partly on the tensor cores with split 16-bit operands).
+ *   harm_index how a harmonic plane is indexed (the paper's "stretch" is not defined):
+ *              FDAS_INDEX_FUNDAMENTAL (default): SP_k(i, j) = FOP(k i, k j), HP_k = HP_{k-1} + SP_k,
+ *                on |k i| <= c, k j <= N-1 (c = (n_temp-1)/2);
+ *              FDAS_INDEX_HIGHEST: (i, j) is the k-th (highest) harmonic, the lower harmonics sit at
+ *                rounded fractions, HP_k(i, j) = sum_{l=1..k} FOP(rd(l i, k), rd(l j, k)) with
+ *                rd(a, b) = round(a / b), halves away from zero, on the whole plane. Not incremental
+ *                in k, so it reads the plane about (n_harm+1)/2 times as often. Not in the batched form.
  */
+#define FDAS_INDEX_FUNDAMENTAL 0
+#define FDAS_INDEX_HIGHEST 1
 typedef struct {
     int32_t n_temp;
     int32_t z_min;
@@ -79,10 +89,12 @@ typedef struct {
     uint32_t harm_mask;
     int32_t cand_cap;
     int32_t precision;
+    int32_t harm_index;
 } fdas_params;
 
-/* One candidate: HP_k(i, j) = power > TA(k, i). i is the fundamental's template offset from the
- * zero-drift row (drift z = i*z_step), j its column (Fourier bin), k the harmonic plane (1-based). */
+/* One candidate: HP_k(i, j) = power > TA(k, i). With FDAS_INDEX_FUNDAMENTAL, i is the fundamental's
+ * template offset from the zero-drift row (drift z = i*z_step) and j its column (Fourier bin); with
+ * FDAS_INDEX_HIGHEST they are those of the k-th harmonic. k is the harmonic plane (1-based). */
 typedef struct {
     float power;
     uint32_t j;
@@ -92,7 +104,7 @@ typedef struct {
 } fdas_cand;
 
 /* Fill *p with the defaults above (85 templates, z = -42..42, 421 taps, F = 2048, 8 planes,
- * all reported, 200 candidates, FP32). */
+ * all reported, 200 candidates, FP32, fundamental indexing). */
 void fdas_default_params(fdas_params *p);
 
 /* FDAS_OK if *p is valid and this build has kernels for it. Otherwise FDAS_ERR_INVALID_ARG or

@@ -14,6 +14,17 @@ with exact integer indices. Row index i is the template offset from the zero-dri
 |i| <= c = (N_temp-1)/2, so FOP(r, j) means plane row c + r. HP_k is defined on the domain
 D_k = {|k*i| <= c, k*j <= N-1}. Points outside D_k are not evaluated.
 
+A second reading, offered as an option (``index="highest"``), indexes every harmonic plane by
+the position of its highest harmonic, as pulsar searches commonly do. The point (i, j) of HP_k is
+taken as the k-th harmonic of a signal, and the lower harmonics l = 1..k sit at l/k of its row
+offset and column, rounded to the nearest integer (halves away from zero):
+
+    HP_k(i, j) = sum_{l=1..k} FOP(rd(l*i, k), rd(l*j, k)),   rd(a, b) = round(a / b),
+
+on the whole plane (|i| <= c, 0 <= j <= N-1), as float32 running sums in the order l = 1..k. It
+is not incremental in k, because the positions change with k. Where k divides both i and j the
+terms are those of the fundamental reading at (i/k, j/k).
+
 Detection emits (k, i, j, HP_k(i, j)) when HP_k(i, j) > TA(k, i), for the harmonics k
 selected by ``harm_mask`` (bit k-1). The test is strict and done in float32. The sums are
 float32 running sums in the order l = 1, 2, ..., k, so a device implementation that adds in
@@ -72,20 +83,51 @@ def harmonic_planes(plane32: np.ndarray, n_harm: int):
             yield k, i, hp
 
 
+def round_div(a, b: int):
+    """round(a / b) for integers a (scalar or array) and b > 0, halves away from zero, exactly."""
+    a = np.asarray(a, dtype=np.int64)
+    return np.sign(a) * ((2 * np.abs(a) + b) // (2 * b))
+
+
+def harmonic_planes_highest(plane32: np.ndarray, n_harm: int):
+    """Yield (k, i, HP_k(i, :)) for k = 1..n_harm and every |i| <= c, indexed by the highest harmonic.
+
+    HP_k(i, j) for j = 0..N-1 is the running float32 sum over l = 1..k of
+    plane[c + rd(l*i, k)][rd(l*j, k)].
+    """
+    p = np.asarray(plane32, dtype=np.float32)
+    n_temp, n = p.shape
+    c = (n_temp - 1) // 2
+    j = np.arange(n, dtype=np.int64)
+    for k in range(1, n_harm + 1):
+        cols = [round_div(l * j, k) for l in range(1, k + 1)]
+        for i in range(-c, c + 1):
+            hp = None
+            for l in range(1, k + 1):
+                v = p[c + int(round_div(l * i, k)), cols[l - 1]]
+                hp = v.copy() if hp is None else (hp + v).astype(np.float32)
+            yield k, i, hp
+
+
 def detect(
     plane32: np.ndarray,
     thresh: np.ndarray,
     n_harm: int,
     harm_mask: int,
     cand_cap: int,
+    index: str = "fundamental",
 ) -> HarmonicResult:
-    """Algorithm 1 over a float32 plane with float32 thresholds TA[k-1][c + i]."""
+    """Algorithm 1 over a float32 plane with float32 thresholds TA[k-1][c + i].
+
+    index: "fundamental" (SP_k(i, j) = FOP(k i, k j)) or "highest" (harmonic_planes_highest).
+    """
     p = np.asarray(plane32, dtype=np.float32)
     ta = np.asarray(thresh, dtype=np.float32)
     c = (p.shape[0] - 1) // 2
     found = {k: ([], [], []) for k in range(1, n_harm + 1)}
     best = {}
-    for k, i, hp in harmonic_planes(p, n_harm):
+    planes = harmonic_planes(p, n_harm) if index == "fundamental" else harmonic_planes_highest(p, n_harm)
+    for k, i, hp in planes:
         # Per-plane peak: the largest value, earliest (i, j) on ties (i is visited ascending).
         jbest = int(np.argmax(hp))
         cur = (hp[jbest], i, jbest)

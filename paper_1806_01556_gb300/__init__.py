@@ -77,6 +77,7 @@ class Params:
     harm_mask: int = 0xFF
     cand_cap: int = 200
     precision: int = _lib.FDAS_FP32
+    harm_index: int = _lib.FDAS_INDEX_FUNDAMENTAL
 
     def c(self) -> _lib.fdas_params:
         return _lib.fdas_params(**asdict(self))

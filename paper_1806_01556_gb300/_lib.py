@@ -19,6 +19,7 @@ FDAS_ERR_CUDA = -4
 FDAS_DEV_WAIT_TIMEOUT = 1
 
 FDAS_FP32, FDAS_BF16X3, FDAS_FP16S = 0, 1, 2
+FDAS_INDEX_FUNDAMENTAL, FDAS_INDEX_HIGHEST = 0, 1
 FDAS_MAX_N = 1 << 24
 FDAS_RAW_CAP = 16384
 FDAS_MAX_CAND_CAP = 4096
@@ -38,6 +39,7 @@ class fdas_params(C.Structure):
         ("harm_mask", C.c_uint32),
         ("cand_cap", C.c_int32),
         ("precision", C.c_int32),
+        ("harm_index", C.c_int32),
     ]
 
 

@@ -58,6 +58,7 @@ void fdas_default_params(fdas_params *p) {
     p->harm_mask = 0xFFu;
     p->cand_cap = 200;
     p->precision = FDAS_FP32;
+    p->harm_index = FDAS_INDEX_FUNDAMENTAL;
 }
 
 fdas_status fdas_check_params(const fdas_params *p) {
@@ -72,6 +73,7 @@ fdas_status fdas_check_params(const fdas_params *p) {
     if (p->cand_cap < 1 || p->cand_cap > FDAS_MAX_CAND_CAP) return FDAS_ERR_INVALID_ARG;
     if (p->precision != FDAS_FP32 && p->precision != FDAS_BF16X3 && p->precision != FDAS_FP16S)
         return FDAS_ERR_INVALID_ARG;
+    if (p->harm_index != FDAS_INDEX_FUNDAMENTAL && p->harm_index != FDAS_INDEX_HIGHEST) return FDAS_ERR_INVALID_ARG;
     if (p->fft_len != 2048) return FDAS_ERR_UNSUPPORTED;
     return FDAS_OK;
 }
@@ -190,7 +192,7 @@ fdas_status fdas_search_convolve(const fdas_params *p, const void *d_spec, size_
     if (e != cudaSuccess) return FDAS_ERR_CUDA;
     const float2 *spec = static_cast<const float2 *>(d_spec);
     const float2 *tmpl = static_cast<const float2 *>(d_tmpl);
-    if (g.precision == FDAS_FP32)
+    if (g.precision == FDAS_FP32 && p->harm_index == FDAS_INDEX_FUNDAMENTAL)
         e = fdas::launch_convolve_hp1(g, spec, n, tmpl, d_plane, ld, d_thresh, p->harm_mask, p->n_harm, ws, stream);
     else
         e = fdas::launch_convolve(g, spec, n, tmpl, d_plane, ld, 0, 0, stream);
@@ -210,7 +212,8 @@ fdas_status fdas_search_harmonic(const fdas_params *p, const float *d_plane, siz
     if (ws_bytes < fdas_workspace_bytes(p, n)) return FDAS_ERR_WORKSPACE;
     const fdas::HsWorkspace ws = fdas::hs_workspace(d_ws, p->n_harm);
     return cuda_status(fdas::launch_harmonic(*p, d_plane, n, ld, d_thresh, d_cands, d_counts, d_peaks, ws, stream,
-                                             /*hp1_done=*/p->precision == FDAS_FP32));
+                                             /*hp1_done=*/p->precision == FDAS_FP32 &&
+                                                 p->harm_index == FDAS_INDEX_FUNDAMENTAL));
 }
 
 fdas_status fdas_search(const fdas_params *p, const void *d_spec, size_t n, const void *d_tmpl, float *d_plane,

@@ -20,6 +20,7 @@ fdas_status check_items(const fdas_params *p, const fdas_batch_item *items, int 
                         const float *d_thresh, void *d_ws, size_t ws_bytes) {
     fdas_status st = fdas_check_params(p);
     if (st != FDAS_OK) return st;
+    if (p->harm_index != FDAS_INDEX_FUNDAMENTAL) return FDAS_ERR_UNSUPPORTED;  // the batched launches index by fundamental
     if (!items || count < 1 || count > FDAS_MAX_BATCH || !d_tmpl || !d_thresh || !d_ws) return FDAS_ERR_INVALID_ARG;
     if (!aligned(d_tmpl, 16) || !aligned(d_ws, 16) || !aligned(d_thresh, 4)) return FDAS_ERR_INVALID_ARG;
     if (ws_bytes < fdas_batch_workspace_bytes(p, count)) return FDAS_ERR_WORKSPACE;

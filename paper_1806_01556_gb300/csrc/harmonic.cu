@@ -256,6 +256,70 @@ __global__ void __launch_bounds__(kHsThreads, KL <= 3 ? 4 : 2)
                counters, peaks);
 }
 
+// ---- highest-harmonic indexing (FDAS_INDEX_HIGHEST) ------------------------------------------------
+// round(a / b) for b > 0, halves away from zero, exactly in integers.
+__device__ __forceinline__ int round_div(int a, int b) {
+    const int m = (2 * (a < 0 ? -a : a) + b) / (2 * b);
+    return a < 0 ? -m : m;
+}
+
+// Every plane k <= n_harm of one row i over kHhCols columns: HP_k(i, j) = sum_{l=1..k} of
+// P[c + rd(l i, k)][rd(l j, k)], float32 running sums in the order l = 1..k. Lane L of warp w takes
+// j = j0 + 32 (kHhJ w + u) + L, u < kHhJ, so for each (k, l) a warp's loads fall on at most 32
+// consecutive columns of one row (rd(l j, k) moves by l/k <= 1 per lane). k and l are compile-time
+// after unrolling, so the divisions become multiplications.
+constexpr int kHhJ = 4;
+constexpr int kHhCols = kHsThreads * kHhJ;  // 1024 columns per CTA
+template <int KMAX>
+__global__ void __launch_bounds__(kHsThreads)
+    fdas_hs_hh(const float *__restrict__ plane, int n, size_t ld, const float *__restrict__ thresh, int n_temp,
+               unsigned mask, int n_harm, unsigned long long *__restrict__ raw, unsigned long long *counters,
+               unsigned long long *peaks) {
+    const int c = (n_temp - 1) / 2;
+    const int row = blockIdx.y, i = row - c;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int jb = blockIdx.x * kHhCols + 32 * kHhJ * warp + lane;
+    unsigned long long key[KMAX];
+#pragma unroll
+    for (int k = 1; k <= KMAX; ++k) {
+        key[k - 1] = 0ull;
+        if (k > n_harm) continue;  // uniform
+        const float ta = ((mask >> (k - 1)) & 1u) ? __ldg(&thresh[(k - 1) * n_temp + row]) : __int_as_float(0x7f800000);
+        float hp[kHhJ];
+#pragma unroll
+        for (int l = 1; l <= k; ++l) {
+            const float *prow = plane + (size_t)(c + round_div(l * i, k)) * ld;
+#pragma unroll
+            for (int u = 0; u < kHhJ; ++u) {
+                const int j = jb + 32 * u;
+                const float v = j < n ? __ldg(prow + (2 * l * j + k) / (2 * k)) : 0.0f;
+                hp[u] = (l == 1) ? v : __fadd_rn(hp[u], v);
+            }
+        }
+        float best = -1.0f;
+        int bestj = 0;
+        bool any_hit = false;
+#pragma unroll
+        for (int u = 0; u < kHhJ; ++u) {
+            const int j = jb + 32 * u;
+            const bool ok = j < n;
+            const bool gt = ok && hp[u] > best;
+            best = gt ? hp[u] : best;
+            bestj = gt ? j : bestj;
+            any_hit |= ok && hp[u] > ta;
+        }
+        if (__any_sync(0xFFFFFFFFu, any_hit)) {
+#pragma unroll
+            for (int u = 0; u < kHhJ; ++u) {
+                const int j = jb + 32 * u;
+                emit(j < n && hp[u] > ta, hp[u], row, (unsigned)j, k, lane, counters, raw);
+            }
+        }
+        key[k - 1] = warp_peak_key(best, bestj, row);
+    }
+    block_peaks<KMAX>(key, peaks);
+}
+
 using HsKernel = void (*)(const float *, int, size_t, const float *, int, unsigned, int, int, unsigned long long *,
                           unsigned long long *, unsigned long long *);
 
@@ -515,6 +579,23 @@ cudaError_t launch_harmonic(const fdas_params &p, const float *plane, size_t n, 
         if (e != cudaSuccess) return e;
     }
     const unsigned mask = p.harm_mask;
+    if (p.harm_index == FDAS_INDEX_HIGHEST) {
+        const dim3 grid((unsigned)((n + kHhCols - 1) / kHhCols), (unsigned)p.n_temp);
+        if (p.n_harm <= 8)
+            fdas_hs_hh<8><<<grid, kHsThreads, 0, s>>>(plane, (int)n, ld, thresh, p.n_temp, mask, p.n_harm, ws.raw,
+                                                      ws.counters, ws.peaks);
+        else
+            fdas_hs_hh<16><<<grid, kHsThreads, 0, s>>>(plane, (int)n, ld, thresh, p.n_temp, mask, p.n_harm, ws.raw,
+                                                       ws.counters, ws.peaks);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        const int smem = FDAS_RAW_CAP * (int)sizeof(unsigned long long);
+        e = cudaFuncSetAttribute(fdas_hs_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        fdas_hs_finalize<<<p.n_harm, kFinThreads, smem, s>>>(ws.raw, ws.counters, ws.peaks, p.n_temp, p.cand_cap,
+                                                              cands, counts, peaks);
+        return cudaGetLastError();
+    }
     // Rows with at least two planes in a few launches (kGroups), then the single-plane rows
     // (|i| > c/2; every row when n_harm = 1) streamed by fdas_hs_k1.
     const int c = (p.n_temp - 1) / 2;

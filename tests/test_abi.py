@@ -43,7 +43,7 @@ def test_every_declared_symbol_is_exported_and_bound(fd):
 def test_struct_layouts_match_header(fd):
     from paper_1806_01556_gb300 import _lib
 
-    assert C.sizeof(_lib.fdas_params) == 36
+    assert C.sizeof(_lib.fdas_params) == 40
     assert C.sizeof(_lib.fdas_cand) == 12
     assert fd.CAND_DTYPE.itemsize == 12
 
@@ -81,6 +81,8 @@ def test_defaults_and_sizes(fd):
         (dict(precision=1, fft_len=4096), -2),
         (dict(precision=1), 0),
         (dict(precision=2), 0),
+        (dict(harm_index=1), 0),
+        (dict(harm_index=2), -1),
         (dict(n_temp=9, z_min=-8, z_step=2), 0),
         (dict(n_harm=16, harm_mask=0xFFFF), 0),
     ],
@@ -185,6 +187,9 @@ def test_batch_arguments_are_checked_on_the_host(fd):
     assert not h.value
     assert lib.fdas_batch_plan_launch(None, None) == -1
     lib.fdas_batch_plan_destroy(None)
+    items[1].d_plane = fake
+    hh = fd.Params(harm_index=1).c()  # the batched launches index by fundamental only
+    assert lib.fdas_search_batch(C.byref(hh), C.cast(items, vp), 2, *args, ws, None, None) == -2
 
 
 def test_server_arguments_are_checked_on_the_host(fd):

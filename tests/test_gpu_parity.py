@@ -363,6 +363,7 @@ def _search_both_ways(fd, p, spec, thresh, ld=None):
         (40000, dict(n_harm=1, harm_mask=1, cand_cap=1000), 3.5),
         (40000, dict(n_harm=16, harm_mask=0xFFFF), 3.5),
         (30000, dict(n_temp=9, z_min=-8, z_step=2, n_tap=129, n_harm=4, harm_mask=0xF), 3.0),
+        (30000, dict(harm_index=1), 3.5),
     ],
 )
 def test_search_with_fused_hp1_equals_separate_calls(fd, n, kw, sigma):
@@ -380,3 +381,53 @@ def test_search_with_fused_hp1_equals_separate_calls(fd, n, kw, sigma):
     assert np.array_equal(ka, kb)
     if p.harm_mask & 1:
         assert int(na[0]) > 0 or n < 64
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("n_tap", [257, 129])
+def test_plane_reduced_taps(fd, prec, n_tap):
+    """The paper's reduced-tap variants (256 and 128 taps, Sec. 4, run as 257 and 129 so that every
+    template stays centred) on the full 85-template grid, every convolution form."""
+    p = fd.Params(n_tap=n_tap, precision=prec)
+    grid = templates.TemplateGrid(n_tap=n_tap)
+    bank = templates.template_bank(grid)
+    spec = synth.small_workload(n=20000).spectrum
+    got, _ = run_convolve(fd, p, spec)
+    mx, rms = plane_rel(got, correlate.plane_ols(spec, bank, 2048))
+    print(f"n_tap={n_tap} precision={prec}: rel max {mx:.2e} rms {rms:.2e}")
+    assert mx <= REL_TOL
+
+
+# ---------------------------------------------------------------- highest-harmonic indexing
+
+
+@pytest.mark.parametrize(
+    "n,kw,sigma",
+    [
+        (7, dict(n_harm=3, harm_mask=0b101), 1.5),
+        (1000, dict(n_harm=4, harm_mask=0xF), 3.0),
+        (4099, {}, 3.5),
+        (20000, dict(n_harm=16, harm_mask=0xFFFF), 4.0),
+        (20000, dict(n_temp=9, z_min=-8, z_step=2, n_harm=8, harm_mask=0b10010110), 3.0),
+    ],
+)
+def test_harmonic_highest_index_bit_exact(fd, n, kw, sigma):
+    """FDAS_INDEX_HIGHEST against the oracle's highest-harmonic planes: candidates, counts and peaks
+    bit for bit on unit-exponential planes."""
+    p = fd.Params(harm_index=1, cand_cap=1000, **kw)
+    plane = synth.exponential_plane(np.random.default_rng(100 + n), p.n_temp, n)
+    ta = thresholds.threshold_array(p.n_harm, p.n_temp, sigma=sigma)
+    got = run_harmonic(fd, p, plane, ta, ld=n + 5)
+    ref = harmonic.detect(plane, ta, p.n_harm, p.harm_mask, p.cand_cap, index="highest")
+    assert_same_candidates(*got, ref, p.harm_mask)
+
+
+def test_harmonic_highest_index_large(fd):
+    """N = 2^18 with the default 85 x 8 planes: counts and candidates against the oracle."""
+    p = fd.Params(harm_index=1, cand_cap=500)
+    n = 1 << 18
+    plane = synth.exponential_plane(np.random.default_rng(7), p.n_temp, n)
+    ta = thresholds.threshold_array(p.n_harm, p.n_temp, sigma=4.5)
+    got = run_harmonic(fd, p, plane, ta)
+    ref = harmonic.detect(plane, ta, p.n_harm, p.harm_mask, p.cand_cap, index="highest")
+    assert_same_candidates(*got, ref, p.harm_mask)

@@ -120,3 +120,88 @@ def test_threshold_matches_scipy_inverse_gamma():
 def test_meansd_threshold_is_literal():
     ta = thresholds.threshold_array(4, 3, sigma=6.0, kind="meansd")
     assert np.allclose(ta[:, 0], [1 + 6, 2 + 6 * math.sqrt(2), 3 + 6 * math.sqrt(3), 4 + 12], rtol=1e-7)
+
+
+# ---------------------------------------------------------------- highest-harmonic indexing
+
+
+def _rd(a, b):
+    """round(a/b), halves away from zero, by exact rational arithmetic (independent of round_div)."""
+    from fractions import Fraction
+
+    x = Fraction(a, b)
+    f = abs(x)
+    n = int(f)
+    if f - n >= Fraction(1, 2):
+        n += 1
+    return n if x >= 0 else -n
+
+
+def test_round_div_matches_exact_rounding():
+    for a in range(-60, 61):
+        for b in range(1, 17):
+            assert int(harmonic.round_div(a, b)) == _rd(a, b), (a, b)
+
+
+def test_highest_harmonic_brute_force():
+    """Every HP_k value on a 7 x 41 plane against a pure-Python sum with exact rounding."""
+    rng = np.random.default_rng(21)
+    plane = rng.exponential(1.0, size=(7, 41)).astype(np.float32)
+    c = 3
+    got = {(k, i): hp for k, i, hp in harmonic.harmonic_planes_highest(plane, 4)}
+    for k in range(1, 5):
+        for i in range(-c, c + 1):
+            for j in range(41):
+                s = np.float32(0)
+                for l in range(1, k + 1):
+                    v = plane[c + _rd(l * i, k), _rd(l * j, k)]
+                    s = v if l == 1 else np.float32(s + v)
+                assert got[(k, i)][j] == s, (k, i, j)
+
+
+def test_highest_harmonic_equals_fundamental_where_k_divides():
+    """Where k divides i and j, the highest-harmonic point (i, j) has the terms of the fundamental
+    point (i/k, j/k): the values agree bit for bit."""
+    rng = np.random.default_rng(22)
+    plane = rng.exponential(1.0, size=(17, 300)).astype(np.float32)
+    c = 8
+    hh = {(k, i): hp for k, i, hp in harmonic.harmonic_planes_highest(plane, 4)}
+    fu = {(k, i): hp for k, i, hp in harmonic.harmonic_planes(plane, 4)}
+    for k in range(1, 5):
+        for i in range(-c, c + 1):
+            if i % k or abs(i) > c:
+                continue
+            f = fu[(k, i // k)]
+            for j in range(0, 300, k):
+                if j // k < f.size:
+                    assert hh[(k, i)][j] == f[j // k], (k, i, j)
+
+
+def test_highest_harmonic_pulse_train_closed_form(bank):
+    """A pulse train (harmonics at multiples of f0, f0 > 2h): at the k-th harmonic position
+    j = k f0 of the zero-drift row, HP_k = k (f0/N)^2, as in the fundamental reading."""
+    n, f0 = 1 << 14, 512
+    spec = synth.pulse_train_spectrum(n, f0)
+    plane = correlate.plane_direct(spec, bank).astype(np.float32)
+    c = (plane.shape[0] - 1) // 2
+    unit = (f0 / n) ** 2
+    for k, i, hp in harmonic.harmonic_planes_highest(plane, 8):
+        if i != 0 or k * f0 >= n:
+            continue
+        assert abs(float(hp[k * f0]) / (k * unit) - 1.0) < 1e-6, k
+        # Between harmonics (211 bins past the k-th) every term is zero.
+        if k * f0 + 211 < n:
+            assert hp[k * f0 + 211] < 1e-12 * unit
+
+
+def test_detect_highest_index_counts_and_order():
+    rng = np.random.default_rng(23)
+    plane = rng.exponential(1.0, size=(9, 500)).astype(np.float32)
+    ta = np.full((4, 9), 6.0, dtype=np.float32)
+    res = harmonic.detect(plane, ta, 4, 0xF, 50, index="highest")
+    allv = {(k, i): hp for k, i, hp in harmonic.harmonic_planes_highest(plane, 4)}
+    for k in range(1, 5):
+        total = sum(int((allv[(k, i)] > ta[k - 1, 0]).sum()) for i in range(-4, 5))
+        assert res.counts[k - 1] == total
+        c = res.cands[k - 1]
+        assert np.all(np.diff(c["power"].astype(np.float64)) <= 0)
