@@ -1,28 +1,31 @@
 // Harmonic summing with threshold detection (Sec. 2.2, Algorithm 1).
 //
-// Stretch read by fundamental: HP_k(i, j) = sum_{l=1..k} P[c + l*i][l*j] on
+// Stretch read by fundamental (the default): HP_k(i, j) = sum_{l=1..k} P[c + l*i][l*j] on
 // D_k = {|k*i| <= c, k*j <= n-1}, summed in float32 in the order l = 1, 2, ..., k. As in the
 // paper's MultipleHP kernels, all planes are computed at once and no HP plane is stored: one
 // thread owns one fundamental (i, j) and keeps the running sum in a register.
 //
 // GB300 mapping:
 //   fdas_hs_reset    zeroes the per-plane crossing counters and peak keys in the workspace.
-//   fdas_hs_k1       one launch for the single-plane rows (|i| > c/2): 16-byte streaming loads,
-//                    4096 columns per CTA.
-//   fdas_hs_kl<KL>   one launch for every row with at least two planes (|i| <= c/2), compiled for
-//                    KL >= n_harm terms; row i caps its terms at K(i) = min(n_harm, floor(c/|i|)).
-//                    A CTA takes 8 chunks of 1024 columns; in each chunk a thread issues every
-//                    strided gather P[c + l i][l j] of its 4 fundamentals before summing, through
-//                    the read-only path, and warps whose columns all have the same number of terms
-//                    skip the per-element domain test.
+//   fdas_hs_k1       the single-plane rows (|i| > c/2): 16-byte streaming loads, 4096 columns per
+//                    CTA. fdas_search with FP32 skips it: the convolution takes those rows' HP_1.
+//   fdas_hs_kl<KL>   the rows with at least two planes (|i| <= c/2) in three launches, by their
+//                    plane count K(i) = min(n_harm, floor(c/|i|)): 5-16, 3-4 and 2 (kGroups), each
+//                    compiled for KL terms with a per-row cap at K(i). A CTA takes 8 chunks of
+//                    256 J columns (J = 8, 6 or 2 fundamentals per thread for up to 4, 8 or 16
+//                    planes); in each chunk a thread issues every strided gather P[c + l i][l j] of
+//                    its J fundamentals before summing, through the read-only path, and warps whose
+//                    columns all have the same number of terms skip the per-element domain test.
 //                    Crossings are rare and take a separate path: a ballot, one atomicAdd per warp,
 //                    and a prefix popcount for each lane's slot. Each candidate
 //                    is one 64-bit key whose ascending order is the canonical order (power desc,
 //                    i asc, j asc). The loudest point of every plane comes from warp reductions
 //                    (redux max of the power bits, then redux min of the column), a block merge in
 //                    shared memory, and at most one 64-bit atomicMax per block and plane.
-//   fdas_hs_finalize one CTA per plane. It bitonic-sorts the raw keys in shared memory, then decodes
-//                    the top cand_cap keys into fdas_cand records and writes the counts and peaks.
+//   fdas_hs_hh<K>    the highest-harmonic indexing (FDAS_INDEX_HIGHEST), one launch over all rows.
+//   fdas_hs_finalize one CTA per plane. A bitonic sort of the raw keys (2, 4 or 16 keys per thread in
+//                    registers, shuffles for the middle strides, shared memory for the largest), then
+//                    the top cand_cap keys decoded into fdas_cand records, the counts and the peaks.
 #include "hs_keys.cuh"
 
 namespace fdas {

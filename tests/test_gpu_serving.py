@@ -37,7 +37,8 @@ def _drain(server, count):
     return done
 
 
-@pytest.mark.parametrize("kw", [dict(), dict(n_harm=16, harm_mask=0xFFFF, cand_cap=64)])
+@pytest.mark.parametrize("kw", [dict(), dict(n_harm=16, harm_mask=0xFFFF, cand_cap=64), dict(precision=1),
+                                dict(precision=2, n_harm=16, harm_mask=0xFFFF, cand_cap=64)])
 def test_server_results_equal_standalone_search(fd, kw):
     p = fd.Params(**kw)
     specs = _spectra(11)
