@@ -41,7 +41,8 @@ typedef int fdas_status;
 #define FDAS_ERR_WORKSPACE (-3)   /* workspace smaller than fdas_workspace_bytes()             */
 #define FDAS_ERR_CUDA (-4)        /* a CUDA runtime call or kernel launch failed               */
 
-/* Arithmetic of the FT convolution. Only FDAS_FP32 has kernels in this build. */
+/* Arithmetic of the FT convolution: plain FP32 FFTs, or part of each inverse DFT as a GEMM on the
+ * tensor cores with 16-bit operands split in two (BF16 halves, or FP16 halves with scaling). */
 #define FDAS_FP32 0
 #define FDAS_BF16X3 1
 #define FDAS_FP16S 2

@@ -22,10 +22,12 @@
 //                    i asc, j asc). The loudest point of every plane comes from warp reductions
 //                    (redux max of the power bits, then redux min of the column), a block merge in
 //                    shared memory, and at most one 64-bit atomicMax per block and plane.
-//   fdas_hs_hh<K>    the highest-harmonic indexing (FDAS_INDEX_HIGHEST), one launch over all rows.
+//   fdas_hs_hh8/16   the highest-harmonic indexing (FDAS_INDEX_HIGHEST), one launch over all rows.
 //   fdas_hs_finalize one CTA per plane. A bitonic sort of the raw keys (2, 4 or 16 keys per thread in
 //                    registers, shuffles for the middle strides, shared memory for the largest), then
 //                    the top cand_cap keys decoded into fdas_cand records, the counts and the peaks.
+#include <type_traits>
+
 #include "hs_keys.cuh"
 
 namespace fdas {
@@ -260,67 +262,361 @@ __global__ void __launch_bounds__(kHsThreads, KL <= 3 ? 4 : 2)
 }
 
 // ---- highest-harmonic indexing (FDAS_INDEX_HIGHEST) ------------------------------------------------
+// HP_k(i, j) = sum_{l=1..k} of P[c + rd(l i, k)][rd(l j, k)], float32 running sums in the order
+// l = 1..k, rd = round half away from zero. A term depends on l/k only as a rational number, so the
+// terms of all planes k <= K come from the reduced fractions q = a/b, b <= K (22 for K = 8, 80 for
+// K = 16): term (l, k) of fundamental (i, j) is P[c + rd(a i, b)][rd(a j, b)] with a/b = l/k in
+// lowest terms.
+//
+// A CTA takes one row i and W fundamental columns [j0, j0 + W). For each fraction it first copies
+// the source columns [rd(a j0, b), rd(a (j0 + W - 1), b)] of row c + rd(a i, b) into its own
+// shared-memory segment with coalesced 16-byte loads; then every plane is summed from the segments.
+// Consecutive threads take consecutive columns, so they read the same or consecutive words of a
+// segment (rd(a j, b) moves by a/b <= 1 per column) and the reads are free of bank conflicts.
+//
+//   fdas_hs_hh8   up to 8 planes. W = 1680 = 4 x 420, thread t < 420 takes j = j0 + t + 420 v, v < 4.
+//                 Because 420 = lcm(1..7) and 1680 divides j0, rd(a j, b) = a j0 / b + rd(a t, b)
+//                 + 420 a v / b exactly for b <= 7: one division per fraction and thread, then every
+//                 term is a shared-memory load at a constant offset. For b = 8 the division is a shift.
+//   fdas_hs_hh16  9 to 16 planes (80 fractions): W = 512, two columns per thread, one division per
+//                 term.
+
+// Greatest common divisor, and the reduced fractions a/b (1 <= a <= b) ordered by b, then a.
+__host__ __device__ constexpr int gcd_c(int x, int y) {
+    while (y != 0) {
+        const int t = x % y;
+        x = y;
+        y = t;
+    }
+    return x;
+}
+__host__ __device__ constexpr int frac_count(int bmax) {
+    int n = 0;
+    for (int b = 1; b <= bmax; ++b)
+        for (int a = 1; a <= b; ++a) n += gcd_c(a, b) == 1 ? 1 : 0;
+    return n;
+}
+// Position of l/k (1 <= l <= k) in that order.
+__host__ __device__ constexpr int frac_index(int l, int k) {
+    const int g = gcd_c(l, k), a = l / g, b = k / g;
+    int n = frac_count(b - 1);
+    for (int x = 1; x < a; ++x) n += gcd_c(x, b) == 1 ? 1 : 0;
+    return n;
+}
+// Fraction number q of that order: denominator and numerator.
+__host__ __device__ constexpr int frac_b(int q) {
+    int b = 1;
+    while (frac_count(b) <= q) ++b;
+    return b;
+}
+__host__ __device__ constexpr int frac_a(int q) {
+    const int b = frac_b(q);
+    int left = q - frac_count(b - 1), a = 0;
+    while (left >= 0) {
+        ++a;
+        if (gcd_c(a, b) == 1) --left;
+    }
+    return a;
+}
+constexpr int kHhMaxFrac = 80;  // frac_count(16)
+static_assert(frac_count(8) == 22 && frac_count(16) == kHhMaxFrac, "Farey counts");
+static_assert(frac_a(0) == 1 && frac_b(0) == 1 && frac_a(3) == 2 && frac_b(3) == 3 && frac_a(21) == 7 &&
+                  frac_b(21) == 8 && frac_index(6, 8) == 5 && frac_a(8) == 3 && frac_b(8) == 5 &&
+                  frac_a(79) == 15 && frac_b(79) == 16,
+              "fraction order");
+
+// round(x / b) for x >= 0, b > 0, halves up (away from zero).
+__host__ __device__ __forceinline__ int rd_pos(int x, int b) { return (2 * x + b) / (2 * b); }
 // round(a / b) for b > 0, halves away from zero, exactly in integers.
-__device__ __forceinline__ int round_div(int a, int b) {
-    const int m = (2 * (a < 0 ? -a : a) + b) / (2 * b);
+__host__ __device__ __forceinline__ int round_div(int a, int b) {
+    const int m = rd_pos(a < 0 ? -a : a, b);
     return a < 0 ? -m : m;
 }
 
-// Every plane k <= n_harm of one row i over kHhCols columns: HP_k(i, j) = sum_{l=1..k} of
-// P[c + rd(l i, k)][rd(l j, k)], float32 running sums in the order l = 1..k. Lane L of warp w takes
-// j = j0 + 32 (kHhJ w + u) + L, u < kHhJ, so for each (k, l) a warp's loads fall on at most 32
-// consecutive columns of one row (rd(l j, k) moves by l/k <= 1 per lane). k and l are compile-time
-// after unrolling, so the divisions become multiplications.
-constexpr int kHhJ = 4;
-constexpr int kHhCols = kHsThreads * kHhJ;  // 1024 columns per CTA
+template <int L, int K>
+struct HhTerm {
+    static constexpr int q = frac_index(L, K), a = frac_a(q), b = frac_b(q);
+};
+// f(std::integral_constant<int, k>) for k = K..KMAX: loop bodies whose index must be a
+// compile-time constant (term offsets, fraction numbers) whatever the size of the body.
+template <int K, int KMAX, class F>
+__device__ __forceinline__ void for_each_k(F &&f) {
+    if constexpr (K <= KMAX) {
+        f(std::integral_constant<int, K>{});
+        for_each_k<K + 1, KMAX>(f);
+    }
+}
+// The running sum of terms 1..L of plane K in the order l = 1..L; term(integral_constant<L>, K).
+template <int K, int L, int V, class Term>
+__device__ __forceinline__ float hh_sum(const Term &term) {
+    const float x = term(std::integral_constant<int, L>{}, std::integral_constant<int, K>{},
+                         std::integral_constant<int, V>{});
+    if constexpr (L == 1)
+        return x;
+    else
+        return __fadd_rn(hh_sum<K, L - 1, V>(term), x);
+}
+
+// Copies source columns [x0, x1] of one fraction (x0 on a 16-byte boundary when vec) into dst, the
+// threads of the CTA each taking whole 16-byte groups (vec) or single floats.
+__device__ __forceinline__ void hh_stage(float *dst, const float *src, int x0, int x1, bool vec, int tid,
+                                         int nthreads) {
+    if (vec) {
+        const int nv = ((x1 - x0) >> 2) + 1;  // ends at or before the row's 16-byte boundary past x1
+#pragma unroll 4
+        for (int e = tid; e < nv; e += nthreads)
+            reinterpret_cast<float4 *>(dst)[e] = __ldg(reinterpret_cast<const float4 *>(src) + e);
+    } else {
+        for (int e = tid; e <= x1 - x0; e += nthreads) dst[e] = __ldg(src + e);
+    }
+}
+
+// The per-thread detection and peak bookkeeping shared by both kernels: hits bit (k - 1) + KMAX u.
 template <int KMAX>
+struct HhTrack {
+    float best[KMAX];
+    int bestj[KMAX];
+    float ta[KMAX];
+    unsigned hits = 0u;
+};
+
+template <int KMAX, int NW, int NV, class Term>
+__device__ __forceinline__ void hh_finish(HhTrack<KMAX> &tr, const Term &term, int n_harm, int row, int lane,
+                                          int jcol0, int jstep, unsigned long long *raw,
+                                          unsigned long long *counters, unsigned long long *peaks) {
+    // Crossings are rare: recompute the same sums for the planes where a lane of the warp crossed.
+    for_each_k<1, KMAX>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        if (k > n_harm) return;
+        unsigned pm = 0u;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) pm |= 1u << (k - 1 + KMAX * v);
+        if (!__any_sync(0xFFFFFFFFu, (tr.hits & pm) != 0u)) return;
+        for_each_k<0, NV - 1>([&](auto vc) {
+            constexpr int v = decltype(vc)::value;
+            const float hp = hh_sum<k, k, v>(term);
+            emit(((tr.hits >> (k - 1 + KMAX * v)) & 1u) != 0u, hp, row, (unsigned)(jcol0 + jstep * v), k, lane,
+                 counters, raw);
+        });
+    });
+    __shared__ unsigned long long warp_key[NW][KMAX];
+    const int warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+        const unsigned long long key = (k < n_harm) ? warp_peak_key(tr.best[k], tr.bestj[k], row) : 0ull;
+        if (lane == 0) warp_key[warp][k] = key;
+    }
+    __syncthreads();
+    if (threadIdx.x < KMAX) {
+        unsigned long long m = 0ull;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) m = warp_key[w][threadIdx.x] > m ? warp_key[w][threadIdx.x] : m;
+        if (m > *(volatile unsigned long long *)&peaks[threadIdx.x]) atomicMax(&peaks[threadIdx.x], m);
+    }
+}
+
+// Plane sums of one column, then the thread's best point and crossings per plane.
+template <int KMAX, int V, class Term>
+__device__ __forceinline__ void hh_column(HhTrack<KMAX> &tr, const Term &term, int n_harm, bool ok, int j) {
+    constexpr int v = V;
+    for_each_k<1, KMAX>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        if (k > n_harm) return;  // uniform
+        const float hp = hh_sum<k, k, V>(term);
+        const bool gt = ok && hp > tr.best[k - 1];
+        tr.best[k - 1] = gt ? hp : tr.best[k - 1];
+        tr.bestj[k - 1] = gt ? j : tr.bestj[k - 1];
+        tr.hits |= (ok && hp > tr.ta[k - 1]) ? 1u << (k - 1 + KMAX * v) : 0u;
+    });
+}
+
+template <int KMAX>
+__device__ __forceinline__ void hh_track_init(HhTrack<KMAX> &tr, const float *__restrict__ thresh, int n_temp,
+                                              unsigned mask, int n_harm, int row) {
+#pragma unroll
+    for (int k = 1; k <= KMAX; ++k) {
+        tr.best[k - 1] = -1.0f;
+        tr.bestj[k - 1] = 0;
+        tr.ta[k - 1] = (k <= n_harm && ((mask >> (k - 1)) & 1u)) ? __ldg(&thresh[(k - 1) * n_temp + row])
+                                                                 : __int_as_float(0x7f800000);
+    }
+}
+
+// ---- up to 8 planes
+constexpr int kHh8Step = 420;                  // lcm(1, ..., 7)
+constexpr int kHh8V = 4;                       // columns per thread
+constexpr int kHh8W = kHh8Step * kHh8V;        // 1680 columns per CTA
+constexpr int kHh8Threads = 448;               // 14 warps; threads 420..447 only stage
+constexpr int kHh8NQ = 22;
+__host__ __device__ constexpr int hh8_seg(int q) {
+    return ((frac_a(q) * kHh8W + frac_b(q) - 1) / frac_b(q) + 8 + 3) & ~3;
+}
+__host__ __device__ constexpr int hh8_off(int q) {
+    int o = 0;
+    for (int x = 0; x < q; ++x) o += hh8_seg(x);
+    return o;
+}
+constexpr int kHh8SmemBytes = hh8_off(kHh8NQ) * 4;
+static_assert(kHh8SmemBytes <= 100 * 1024, "two CTAs per SM");
+
+// Fraction q's segment: source columns [x0, x1] of row c + rd(a i, b), x0 on a 16-byte boundary.
+struct HhSpan {
+    const float *src;
+    int x0, x1;
+};
+__device__ __forceinline__ HhSpan hh_span(const float *plane, size_t ld, int c, int i, int j0, int jl, int a, int b) {
+    const int x0 = rd_pos(a * j0, b) & ~3;
+    return {plane + (size_t)(c + round_div(a * i, b)) * ld + x0, x0, rd_pos(a * jl, b)};
+}
+
+// Compile-time table of the 22 fractions' numerators, denominators and segment offsets.
+struct Hh8Frac {
+    unsigned char a[kHh8NQ], b[kHh8NQ];
+    int off[kHh8NQ];
+    __host__ __device__ constexpr Hh8Frac() : a{}, b{}, off{} {
+        for (int q = 0; q < kHh8NQ; ++q) {
+            a[q] = (unsigned char)frac_a(q);
+            b[q] = (unsigned char)frac_b(q);
+            off[q] = hh8_off(q);
+        }
+    }
+};
+__constant__ Hh8Frac c_hh8;
+
+template <int Q>
+__device__ __forceinline__ void hh8_divide(int (&r)[kHh8NQ], int t, int j0, int n_harm) {
+    if constexpr (Q < kHh8NQ) {
+        constexpr int a = frac_a(Q), b = frac_b(Q);
+        if (b <= n_harm) {
+            if constexpr (b <= 7)
+                r[Q] = (int)((unsigned)(2 * a * t + b) / (unsigned)(2 * b));  // rd(a t, b)
+            else
+                r[Q] = hh8_off(Q) - (rd_pos(a * j0, b) & ~3);  // segment offset minus its first column
+        }
+        hh8_divide<Q + 1>(r, t, j0, n_harm);
+    }
+}
+
+__global__ void __launch_bounds__(kHh8Threads, 2)
+    fdas_hs_hh8(const float *__restrict__ plane, int n, size_t ld, bool vec, const float *__restrict__ thresh,
+                int n_temp, unsigned mask, int n_harm, unsigned long long *__restrict__ raw,
+                unsigned long long *counters, unsigned long long *peaks) {
+    extern __shared__ float4 hh_seg4[];
+    const float *const S = reinterpret_cast<const float *>(hh_seg4);
+    const int c = (n_temp - 1) / 2;
+    const int row = blockIdx.y, i = row - c;
+    const int lane = threadIdx.x & 31;
+    const int j0 = blockIdx.x * kHh8W;
+    const int jl = min(j0 + kHh8W - 1, n - 1);
+    // Staging: warp w copies fractions w and w + 14 (b <= n_harm), its lanes taking 16-byte groups.
+    for (int q = threadIdx.x >> 5; q < kHh8NQ; q += kHh8Threads / 32) {
+        const int b = c_hh8.b[q];
+        if (b > n_harm) continue;  // warp-uniform
+        const HhSpan sp = hh_span(plane, ld, c, i, j0, jl, c_hh8.a[q], b);
+        hh_stage(reinterpret_cast<float *>(hh_seg4) + c_hh8.off[q], sp.src, sp.x0, sp.x1, vec, lane, 32);
+    }
+    HhTrack<8> tr;
+    hh_track_init<8>(tr, thresh, n_temp, mask, n_harm, row);
+    const bool act = threadIdx.x < kHh8Step;
+    const int t = act ? threadIdx.x : 0;  // idle threads read inside the segments
+    int r[kHh8NQ];
+    hh8_divide<0>(r, t, j0, n_harm);
+    __syncthreads();
+
+    // Term (l, k) of column v: for b <= 7 one load at a constant offset from r[q]; for b = 8 a shift.
+    auto term = [&](auto lc, auto kc, auto vc) -> float {
+        using T = HhTerm<decltype(lc)::value, decltype(kc)::value>;
+        constexpr int v = decltype(vc)::value;
+        if constexpr (T::b <= 7)
+            return S[r[T::q] + (hh8_off(T::q) + kHh8Step * T::a * v / T::b)];
+        else
+            return S[r[T::q] + ((2 * T::a * (j0 + t + kHh8Step * v) + 8) >> 4)];
+    };
+    auto columns = [&](auto full) {
+        for_each_k<0, kHh8V - 1>([&](auto vc) {
+            constexpr int v = decltype(vc)::value;
+            const int j = j0 + t + kHh8Step * v;
+            hh_column<8, v>(tr, term, n_harm, act && (decltype(full)::value || j < n), j);
+        });
+    };
+    if (j0 + kHh8W <= n)
+        columns(std::true_type{});
+    else
+        columns(std::false_type{});
+    hh_finish<8, kHh8Threads / 32, kHh8V>(tr, term, n_harm, row, lane, j0 + t, kHh8Step, raw, counters, peaks);
+}
+
+// ---- 9 to 16 planes
+constexpr int kHh16J = 2;
+constexpr int kHh16W = kHsThreads * kHh16J;  // 512 columns per CTA
+__host__ __device__ constexpr int hh16_seg(int q) {
+    return ((frac_a(q) * kHh16W + frac_b(q) - 1) / frac_b(q) + 8 + 3) & ~3;
+}
+__host__ __device__ constexpr int hh16_off(int q) {
+    int o = 0;
+    for (int x = 0; x < q; ++x) o += hh16_seg(x);
+    return o;
+}
+
+// Segment offsets and first columns per launch, for the fractions with b <= n_harm.
+struct HhTable {
+    int nq;
+    int smem_floats;
+    unsigned char a[kHhMaxFrac], b[kHhMaxFrac];
+    int off[kHhMaxFrac];
+};
+
+HhTable hh16_table(int n_harm) {
+    HhTable t{};
+    for (int q = 0; q < kHhMaxFrac && frac_b(q) <= n_harm; ++q) {
+        t.a[q] = (unsigned char)frac_a(q);
+        t.b[q] = (unsigned char)frac_b(q);
+        t.off[q] = hh16_off(q);
+        t.nq = q + 1;
+    }
+    t.smem_floats = hh16_off(t.nq);
+    return t;
+}
+
 __global__ void __launch_bounds__(kHsThreads)
-    fdas_hs_hh(const float *__restrict__ plane, int n, size_t ld, const float *__restrict__ thresh, int n_temp,
-               unsigned mask, int n_harm, unsigned long long *__restrict__ raw, unsigned long long *counters,
-               unsigned long long *peaks) {
+    fdas_hs_hh16(const float *__restrict__ plane, int n, size_t ld, bool vec, const float *__restrict__ thresh,
+                 int n_temp, unsigned mask, int n_harm, const __grid_constant__ HhTable tab,
+                 unsigned long long *__restrict__ raw, unsigned long long *counters, unsigned long long *peaks) {
+    extern __shared__ float4 hh_seg4[];
+    const float *const S = reinterpret_cast<const float *>(hh_seg4);
+    __shared__ int s_adj[kHhMaxFrac];  // segment offset minus the segment's first column
     const int c = (n_temp - 1) / 2;
     const int row = blockIdx.y, i = row - c;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int jb = blockIdx.x * kHhCols + 32 * kHhJ * warp + lane;
-    unsigned long long key[KMAX];
-#pragma unroll
-    for (int k = 1; k <= KMAX; ++k) {
-        key[k - 1] = 0ull;
-        if (k > n_harm) continue;  // uniform
-        const float ta = ((mask >> (k - 1)) & 1u) ? __ldg(&thresh[(k - 1) * n_temp + row]) : __int_as_float(0x7f800000);
-        float hp[kHhJ];
-#pragma unroll
-        for (int l = 1; l <= k; ++l) {
-            const float *prow = plane + (size_t)(c + round_div(l * i, k)) * ld;
-#pragma unroll
-            for (int u = 0; u < kHhJ; ++u) {
-                const int j = jb + 32 * u;
-                const float v = j < n ? __ldg(prow + (2 * l * j + k) / (2 * k)) : 0.0f;
-                hp[u] = (l == 1) ? v : __fadd_rn(hp[u], v);
-            }
-        }
-        float best = -1.0f;
-        int bestj = 0;
-        bool any_hit = false;
-#pragma unroll
-        for (int u = 0; u < kHhJ; ++u) {
-            const int j = jb + 32 * u;
-            const bool ok = j < n;
-            const bool gt = ok && hp[u] > best;
-            best = gt ? hp[u] : best;
-            bestj = gt ? j : bestj;
-            any_hit |= ok && hp[u] > ta;
-        }
-        if (__any_sync(0xFFFFFFFFu, any_hit)) {
-#pragma unroll
-            for (int u = 0; u < kHhJ; ++u) {
-                const int j = jb + 32 * u;
-                emit(j < n && hp[u] > ta, hp[u], row, (unsigned)j, k, lane, counters, raw);
-            }
-        }
-        key[k - 1] = warp_peak_key(best, bestj, row);
+    const int j0 = blockIdx.x * kHh16W;
+    const int jl = min(j0 + kHh16W - 1, n - 1);
+    // One warp per fraction, fractions dealt out round robin.
+    for (int q = warp; q < tab.nq; q += kHsWarps) {
+        const HhSpan sp = hh_span(plane, ld, c, i, j0, jl, tab.a[q], tab.b[q]);
+        if (lane == 0) s_adj[q] = tab.off[q] - sp.x0;
+        hh_stage(reinterpret_cast<float *>(hh_seg4) + tab.off[q], sp.src, sp.x0, sp.x1, vec, lane, 32);
     }
-    block_peaks<KMAX>(key, peaks);
+    HhTrack<16> tr;
+    hh_track_init<16>(tr, thresh, n_temp, mask, n_harm, row);
+    __syncthreads();
+    const int jb = j0 + 32 * (kHh16J * warp) + lane;
+    auto term = [&](auto lc, auto kc, auto vc) -> float {
+        using T = HhTerm<decltype(lc)::value, decltype(kc)::value>;
+        const int j = min(jb + 32 * decltype(vc)::value, jl);  // keeps the reads inside the staged columns
+        return S[s_adj[T::q] + (int)((unsigned)(2 * T::a * j + T::b) / (unsigned)(2 * T::b))];
+    };
+    auto columns = [&](auto full) {
+        for_each_k<0, kHh16J - 1>([&](auto vc) {
+            constexpr int v = decltype(vc)::value;
+            const int j = jb + 32 * v;
+            hh_column<16, v>(tr, term, n_harm, decltype(full)::value || j < n, j);
+        });
+    };
+    if (j0 + kHh16W <= n)
+        columns(std::true_type{});
+    else
+        columns(std::false_type{});
+    hh_finish<16, kHsWarps, kHh16J>(tr, term, n_harm, row, lane, jb, 32, raw, counters, peaks);
 }
 
 using HsKernel = void (*)(const float *, int, size_t, const float *, int, unsigned, int, int, unsigned long long *,
@@ -583,13 +879,22 @@ cudaError_t launch_harmonic(const fdas_params &p, const float *plane, size_t n, 
     }
     const unsigned mask = p.harm_mask;
     if (p.harm_index == FDAS_INDEX_HIGHEST) {
-        const dim3 grid((unsigned)((n + kHhCols - 1) / kHhCols), (unsigned)p.n_temp);
-        if (p.n_harm <= 8)
-            fdas_hs_hh<8><<<grid, kHsThreads, 0, s>>>(plane, (int)n, ld, thresh, p.n_temp, mask, p.n_harm, ws.raw,
-                                                      ws.counters, ws.peaks);
-        else
-            fdas_hs_hh<16><<<grid, kHsThreads, 0, s>>>(plane, (int)n, ld, thresh, p.n_temp, mask, p.n_harm, ws.raw,
-                                                       ws.counters, ws.peaks);
+        const bool vec = (ld & 3) == 0 && (reinterpret_cast<uintptr_t>(plane) & 15) == 0;
+        if (p.n_harm <= 8) {
+            const dim3 grid((unsigned)((n + kHh8W - 1) / kHh8W), (unsigned)p.n_temp);
+            e = cudaFuncSetAttribute(fdas_hs_hh8, cudaFuncAttributeMaxDynamicSharedMemorySize, kHh8SmemBytes);
+            if (e != cudaSuccess) return e;
+            fdas_hs_hh8<<<grid, kHh8Threads, kHh8SmemBytes, s>>>(plane, (int)n, ld, vec, thresh, p.n_temp, mask,
+                                                                 p.n_harm, ws.raw, ws.counters, ws.peaks);
+        } else {
+            const HhTable tab = hh16_table(p.n_harm);
+            const int smem_hh = tab.smem_floats * (int)sizeof(float);
+            const dim3 grid((unsigned)((n + kHh16W - 1) / kHh16W), (unsigned)p.n_temp);
+            e = cudaFuncSetAttribute(fdas_hs_hh16, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_hh);
+            if (e != cudaSuccess) return e;
+            fdas_hs_hh16<<<grid, kHsThreads, smem_hh, s>>>(plane, (int)n, ld, vec, thresh, p.n_temp, mask, p.n_harm,
+                                                           tab, ws.raw, ws.counters, ws.peaks);
+        }
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         const int smem = FDAS_RAW_CAP * (int)sizeof(unsigned long long);

@@ -402,22 +402,26 @@ def test_plane_reduced_taps(fd, prec, n_tap):
 
 
 @pytest.mark.parametrize(
-    "n,kw,sigma",
+    "n,kw,sigma,aligned",
     [
-        (7, dict(n_harm=3, harm_mask=0b101), 1.5),
-        (1000, dict(n_harm=4, harm_mask=0xF), 3.0),
-        (4099, {}, 3.5),
-        (20000, dict(n_harm=16, harm_mask=0xFFFF), 4.0),
-        (20000, dict(n_temp=9, z_min=-8, z_step=2, n_harm=8, harm_mask=0b10010110), 3.0),
+        (7, dict(n_harm=3, harm_mask=0b101), 1.5, False),
+        (1000, dict(n_harm=4, harm_mask=0xF), 3.0, False),
+        (4099, {}, 3.5, False),
+        (4099, {}, 3.5, True),
+        (20000, dict(n_harm=16, harm_mask=0xFFFF), 4.0, False),
+        (20000, dict(n_harm=16, harm_mask=0xFFFF), 4.0, True),
+        (3001, dict(n_harm=11, harm_mask=0x7FF), 3.0, True),
+        (20000, dict(n_temp=9, z_min=-8, z_step=2, n_harm=8, harm_mask=0b10010110), 3.0, False),
     ],
 )
-def test_harmonic_highest_index_bit_exact(fd, n, kw, sigma):
+def test_harmonic_highest_index_bit_exact(fd, n, kw, sigma, aligned):
     """FDAS_INDEX_HIGHEST against the oracle's highest-harmonic planes: candidates, counts and peaks
-    bit for bit on unit-exponential planes."""
+    bit for bit on unit-exponential planes; with a row stride that allows 16-byte loads and one that
+    does not."""
     p = fd.Params(harm_index=1, cand_cap=1000, **kw)
     plane = synth.exponential_plane(np.random.default_rng(100 + n), p.n_temp, n)
     ta = thresholds.threshold_array(p.n_harm, p.n_temp, sigma=sigma)
-    got = run_harmonic(fd, p, plane, ta, ld=n + 5)
+    got = run_harmonic(fd, p, plane, ta, ld=(n + 63) // 64 * 64 if aligned else n + 5)
     ref = harmonic.detect(plane, ta, p.n_harm, p.harm_mask, p.cand_cap, index="highest")
     assert_same_candidates(*got, ref, p.harm_mask)
 
