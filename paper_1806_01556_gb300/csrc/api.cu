@@ -45,6 +45,23 @@ double gamma_threshold(int k, double p) {
 
 }  // namespace
 
+fdas_status fdas::harmonic_sum_checked(const fdas_params *p, const float *d_plane, size_t n, size_t ld,
+                                       const float *d_thresh, fdas_cand *d_cands, uint32_t *d_counts,
+                                       fdas_cand *d_peaks, void *d_ws, size_t ws_bytes, cudaStream_t stream,
+                                       bool concurrent) {
+    fdas_status st = fdas_check_params(p);
+    if (st != FDAS_OK) return st;
+    if ((st = check_shape(p, n, ld)) != FDAS_OK) return st;
+    if (!d_plane || !d_thresh || !d_cands || !d_counts || !d_ws) return FDAS_ERR_INVALID_ARG;
+    if (!aligned16(d_plane) || !aligned16(d_ws) || ((uintptr_t)d_thresh & 3u) || ((uintptr_t)d_cands & 3u) ||
+        ((uintptr_t)d_counts & 3u) || ((uintptr_t)d_peaks & 3u))
+        return FDAS_ERR_INVALID_ARG;
+    if (ws_bytes < fdas_workspace_bytes(p, n)) return FDAS_ERR_WORKSPACE;
+    const fdas::HsWorkspace ws = fdas::hs_workspace(d_ws, p->n_harm);
+    return cuda_status(fdas::launch_harmonic(*p, d_plane, n, ld, d_thresh, d_cands, d_counts, d_peaks, ws, stream,
+                                             false, concurrent));
+}
+
 extern "C" {
 
 void fdas_default_params(fdas_params *p) {
@@ -163,17 +180,8 @@ fdas_status fdas_convolve(const fdas_params *p, const void *d_spec, size_t n, co
 fdas_status fdas_harmonic_sum(const fdas_params *p, const float *d_plane, size_t n, size_t ld, const float *d_thresh,
                               fdas_cand *d_cands, uint32_t *d_counts, fdas_cand *d_peaks, void *d_ws, size_t ws_bytes,
                               fdas_stream_t stream) {
-    fdas_status st = fdas_check_params(p);
-    if (st != FDAS_OK) return st;
-    if ((st = check_shape(p, n, ld)) != FDAS_OK) return st;
-    if (!d_plane || !d_thresh || !d_cands || !d_counts || !d_ws) return FDAS_ERR_INVALID_ARG;
-    if (!aligned16(d_plane) || !aligned16(d_ws) || ((uintptr_t)d_thresh & 3u) || ((uintptr_t)d_cands & 3u) ||
-        ((uintptr_t)d_counts & 3u) || ((uintptr_t)d_peaks & 3u))
-        return FDAS_ERR_INVALID_ARG;
-    if (ws_bytes < fdas_workspace_bytes(p, n)) return FDAS_ERR_WORKSPACE;
-    const fdas::HsWorkspace ws = fdas::hs_workspace(d_ws, p->n_harm);
-    return cuda_status(
-        fdas::launch_harmonic(*p, d_plane, n, ld, d_thresh, d_cands, d_counts, d_peaks, ws, stream));
+    return fdas::harmonic_sum_checked(p, d_plane, n, ld, d_thresh, d_cands, d_counts, d_peaks, d_ws, ws_bytes, stream,
+                                      true);
 }
 
 fdas_status fdas_search_convolve(const fdas_params *p, const void *d_spec, size_t n, const void *d_tmpl,

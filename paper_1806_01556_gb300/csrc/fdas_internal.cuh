@@ -122,10 +122,15 @@ int convolve_items(const Geometry &g, size_t n, int templates_per_item);
 cudaError_t launch_convolve_batch(const Geometry &g, const ConvBatch &batch, const float2 *tmpl, int grid,
                                   int templates_per_item, cudaStream_t s);
 // Harmonic sum. With hp1_done the workspace was reset before the convolution, which already took
-// HP_1 of the single-plane rows (launch_convolve_hp1).
+// HP_1 of the single-plane rows (launch_convolve_hp1). With concurrent the row-group launches run
+// side by side on two auxiliary streams of the library (created once per device).
 cudaError_t launch_harmonic(const fdas_params &p, const float *plane, size_t n, size_t ld,
                             const float *thresh, fdas_cand *cands, uint32_t *counts, fdas_cand *peaks,
-                            const HsWorkspace &ws, cudaStream_t s, bool hp1_done = false);
+                            const HsWorkspace &ws, cudaStream_t s, bool hp1_done = false, bool concurrent = true);
+// fdas_harmonic_sum with the choice of concurrent launches (fdas_harmonic_sum_noalloc: none).
+fdas_status harmonic_sum_checked(const fdas_params *p, const float *d_plane, size_t n, size_t ld,
+                                 const float *d_thresh, fdas_cand *d_cands, uint32_t *d_counts, fdas_cand *d_peaks,
+                                 void *d_ws, size_t ws_bytes, cudaStream_t stream, bool concurrent);
 // Batched harmonic sum: reset, one launch per group of rows over every spectrum, finalize.
 void harmonic_blocks(const fdas_params &p, size_t n, int *blocks_16k, int *blocks_12k, int *blocks_4k);
 cudaError_t prepare_harmonic_batch();

@@ -23,9 +23,12 @@
 //                    (redux max of the power bits, then redux min of the column), a block merge in
 //                    shared memory, and at most one 64-bit atomicMax per block and plane.
 //   fdas_hs_hh8/16   the highest-harmonic indexing (FDAS_INDEX_HIGHEST), one launch over all rows.
+//   The row-group launches (and fdas_hs_k1) are independent, so they run side by side on the
+//   caller's stream and two auxiliary streams of the library, forked and joined with events.
 //   fdas_hs_finalize one CTA per plane. A bitonic sort of the raw keys (2, 4 or 16 keys per thread in
 //                    registers, shuffles for the middle strides, shared memory for the largest), then
 //                    the top cand_cap keys decoded into fdas_cand records, the counts and the peaks.
+#include <mutex>
 #include <type_traits>
 
 #include "hs_keys.cuh"
@@ -867,9 +870,34 @@ cudaError_t launch_hs_reset(const fdas_params &p, const HsWorkspace &ws, cudaStr
     return cudaGetLastError();
 }
 
+// Two auxiliary streams per device for the concurrent row-group launches, created on first use and
+// kept for the life of the process.
+constexpr int kMaxAuxDevices = 128;
+std::mutex g_aux_mutex;
+cudaStream_t g_aux[kMaxAuxDevices][2];
+
+cudaError_t aux_streams(cudaStream_t *out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxAuxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_aux_mutex);
+    for (int k = 0; k < 2; ++k) {
+        if (g_aux[dev][k] == nullptr) {
+            e = cudaStreamCreateWithFlags(&g_aux[dev][k], cudaStreamNonBlocking);
+            if (e != cudaSuccess) {
+                g_aux[dev][k] = nullptr;
+                return e;
+            }
+        }
+        out[k] = g_aux[dev][k];
+    }
+    return cudaSuccess;
+}
+
 cudaError_t launch_harmonic(const fdas_params &p, const float *plane, size_t n, size_t ld, const float *thresh,
                             fdas_cand *cands, uint32_t *counts, fdas_cand *peaks, const HsWorkspace &ws,
-                            cudaStream_t s, bool hp1_done) {
+                            cudaStream_t s, bool hp1_done, bool concurrent) {
     // hp1_done: the workspace was reset before the convolution, which also took the HP_1 candidates
     // and peak of the single-plane rows; no single-plane launch runs then.
     cudaError_t e = cudaSuccess;
@@ -908,24 +936,59 @@ cudaError_t launch_harmonic(const fdas_params &p, const float *plane, size_t n, 
     // (|i| > c/2; every row when n_harm = 1) streamed by fdas_hs_k1.
     const int c = (p.n_temp - 1) / 2;
     const int lo1 = p.n_harm >= 2 ? c / 2 + 1 : 0;
+    struct Launch {
+        HsKernel kernel;  // nullptr: fdas_hs_k1
+        dim3 grid;
+        int lo;
+    };
+    Launch L[4];
+    int nl = 0;
     for (const Group &gr : kGroups) {
         int lo, hi;
         if (!group_rows(c, p.n_harm, gr.kmin, gr.kmax, &lo, &hi)) continue;
         const int kmax = gr.kmax < p.n_harm ? gr.kmax : p.n_harm;
         const int per = kChunks * kHsThreads * kl_width(kmax);
         const int rows = (lo == 0) ? 2 * hi + 1 : 2 * (hi - lo + 1);
-        hs_kernel(kmax)<<<dim3((unsigned)((n + per - 1) / per), (unsigned)rows), kHsThreads, 0, s>>>(
-            plane, (int)n, ld, thresh, p.n_temp, mask, p.n_harm, lo, ws.raw, ws.counters, ws.peaks);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
+        L[nl++] = {hs_kernel(kmax), dim3((unsigned)((n + per - 1) / per), (unsigned)rows), lo};
     }
     const int rows1 = lo1 == 0 ? 2 * c + 1 : 2 * (c - lo1 + 1);
-    if (rows1 > 0 && !hp1_done) {
-        fdas_hs_k1<<<dim3((unsigned)((n + kK1Cols - 1) / kK1Cols), (unsigned)rows1), kHsThreads, 0, s>>>(
-            plane, (int)n, ld, thresh, p.n_temp, p.harm_mask, lo1, ws.raw, ws.counters, ws.peaks);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
+    if (rows1 > 0 && !hp1_done)
+        L[nl++] = {nullptr, dim3((unsigned)((n + kK1Cols - 1) / kK1Cols), (unsigned)rows1), lo1};
+    // The launches are independent (they only add to the workspace's counters, keys and peaks
+    // atomically). With `concurrent` they run side by side on the caller's stream and two auxiliary
+    // ones, forked from and joined back into the caller's stream by events, so that one launch's
+    // tail overlaps the others' work; the finalize then runs on the caller's stream.
+    cudaStream_t st[3] = {s, s, s};
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    const bool fork = concurrent && nl >= 2;
+    if (fork) {
+        e = aux_streams(&st[1]);
+        for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[0], s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st[1], ev[0], 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st[2], ev[0], 0);
     }
+    for (int k = 0; k < nl && e == cudaSuccess; ++k) {
+        // The largest launch stays on the caller's stream; the single-plane launch follows the
+        // 3-4-plane group on the first auxiliary stream.
+        cudaStream_t sk = fork ? st[k == 0 ? 0 : k == 1 || k == 3 ? 1 : 2] : s;
+        if (L[k].kernel)
+            L[k].kernel<<<L[k].grid, kHsThreads, 0, sk>>>(plane, (int)n, ld, thresh, p.n_temp, mask, p.n_harm, L[k].lo,
+                                                          ws.raw, ws.counters, ws.peaks);
+        else
+            fdas_hs_k1<<<L[k].grid, kHsThreads, 0, sk>>>(plane, (int)n, ld, thresh, p.n_temp, p.harm_mask, L[k].lo,
+                                                         ws.raw, ws.counters, ws.peaks);
+        e = cudaGetLastError();
+    }
+    if (fork) {
+        if (e == cudaSuccess) e = cudaEventRecord(ev[1], st[1]);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[2], st[2]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[1], 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[2], 0);
+        for (int k = 0; k < 3; ++k)
+            if (ev[k]) cudaEventDestroy(ev[k]);  // released once the work that uses them completes
+    }
+    if (e != cudaSuccess) return e;
     const int smem = FDAS_RAW_CAP * (int)sizeof(unsigned long long);
     e = cudaFuncSetAttribute(fdas_hs_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;

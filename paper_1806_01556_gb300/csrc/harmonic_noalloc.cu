@@ -51,6 +51,7 @@ extern "C" fdas_status fdas_harmonic_sum_noalloc(const fdas_params *p, const flo
     if (scratch_address(&ws) != cudaSuccess) return FDAS_ERR_CUDA;
     // The harmonic-sum launch sequence zeroes the counters and peak keys before its main kernel,
     // so whatever an earlier call left in the array does not leak into this one.
-    return fdas_harmonic_sum(p, d_plane, n, ld, d_thresh, d_cands, d_counts, d_peaks, ws,
-                             FDAS_NOALLOC_SCRATCH_BYTES, stream);
+    // One stream only: the concurrent form would create the library's auxiliary streams.
+    return fdas::harmonic_sum_checked(p, d_plane, n, ld, d_thresh, d_cands, d_counts, d_peaks, ws,
+                                      FDAS_NOALLOC_SCRATCH_BYTES, stream, false);
 }
