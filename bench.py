@@ -47,8 +47,8 @@ KERNEL_SOURCES = {
 NCU_TRAFFIC = {
     "convolve.cu": ("9a245990738a", 773.1e6),
     "convolve_tc.cu": ("c7934a72a93f", 669.6e6),
-    "harmonic.cu": ("064a836a2832", 1487.5e6),
-    "harmonic.cu+k1": ("064a836a2832", 1840.0e6),
+    "harmonic.cu": ("b3cfb693ab15", 1487.3e6),
+    "harmonic.cu+k1": ("b3cfb693ab15", 1839.8e6),
 }
 
 
