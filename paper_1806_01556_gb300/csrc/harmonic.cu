@@ -895,6 +895,38 @@ cudaError_t aux_streams(cudaStream_t *out) {
     return cudaSuccess;
 }
 
+// Enqueues launch(k, stream) for k < count. The launches must be independent of one another. With
+// concurrent (and two or more launches) they run side by side: k = 0 on s, k = 1 and 3 on the first
+// auxiliary stream, k = 2 on the second, forked from s and joined back into it by events, so that
+// one launch's tail overlaps the others' work. Work enqueued on s afterwards waits for all of them.
+template <class F>
+cudaError_t side_by_side(cudaStream_t s, int count, bool concurrent, F &&launch) {
+    const bool fork = concurrent && count >= 2;
+    cudaStream_t st[3] = {s, s, s};
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    cudaError_t e = cudaSuccess;
+    if (fork) {
+        e = aux_streams(&st[1]);
+        for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[0], s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st[1], ev[0], 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st[2], ev[0], 0);
+    }
+    for (int k = 0; k < count && e == cudaSuccess; ++k) {
+        launch(k, fork ? st[k == 0 ? 0 : (k & 1) ? 1 : 2] : s);
+        e = cudaGetLastError();
+    }
+    if (fork) {
+        if (e == cudaSuccess) e = cudaEventRecord(ev[1], st[1]);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[2], st[2]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[1], 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[2], 0);
+        for (int k = 0; k < 3; ++k)
+            if (ev[k]) cudaEventDestroy(ev[k]);  // released once the work that uses them completes
+    }
+    return e;
+}
+
 cudaError_t launch_harmonic(const fdas_params &p, const float *plane, size_t n, size_t ld, const float *thresh,
                             fdas_cand *cands, uint32_t *counts, fdas_cand *peaks, const HsWorkspace &ws,
                             cudaStream_t s, bool hp1_done, bool concurrent) {
@@ -954,40 +986,16 @@ cudaError_t launch_harmonic(const fdas_params &p, const float *plane, size_t n, 
     const int rows1 = lo1 == 0 ? 2 * c + 1 : 2 * (c - lo1 + 1);
     if (rows1 > 0 && !hp1_done)
         L[nl++] = {nullptr, dim3((unsigned)((n + kK1Cols - 1) / kK1Cols), (unsigned)rows1), lo1};
-    // The launches are independent (they only add to the workspace's counters, keys and peaks
-    // atomically). With `concurrent` they run side by side on the caller's stream and two auxiliary
-    // ones, forked from and joined back into the caller's stream by events, so that one launch's
-    // tail overlaps the others' work; the finalize then runs on the caller's stream.
-    cudaStream_t st[3] = {s, s, s};
-    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
-    const bool fork = concurrent && nl >= 2;
-    if (fork) {
-        e = aux_streams(&st[1]);
-        for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventRecord(ev[0], s);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(st[1], ev[0], 0);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(st[2], ev[0], 0);
-    }
-    for (int k = 0; k < nl && e == cudaSuccess; ++k) {
-        // The largest launch stays on the caller's stream; the single-plane launch follows the
-        // 3-4-plane group on the first auxiliary stream.
-        cudaStream_t sk = fork ? st[k == 0 ? 0 : k == 1 || k == 3 ? 1 : 2] : s;
+    // The launches are independent: they only add to the workspace's counters, keys and peak keys
+    // atomically. The largest (the first group) stays on the caller's stream.
+    e = side_by_side(s, nl, concurrent, [&](int k, cudaStream_t sk) {
         if (L[k].kernel)
             L[k].kernel<<<L[k].grid, kHsThreads, 0, sk>>>(plane, (int)n, ld, thresh, p.n_temp, mask, p.n_harm, L[k].lo,
                                                           ws.raw, ws.counters, ws.peaks);
         else
             fdas_hs_k1<<<L[k].grid, kHsThreads, 0, sk>>>(plane, (int)n, ld, thresh, p.n_temp, p.harm_mask, L[k].lo,
                                                          ws.raw, ws.counters, ws.peaks);
-        e = cudaGetLastError();
-    }
-    if (fork) {
-        if (e == cudaSuccess) e = cudaEventRecord(ev[1], st[1]);
-        if (e == cudaSuccess) e = cudaEventRecord(ev[2], st[2]);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[1], 0);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[2], 0);
-        for (int k = 0; k < 3; ++k)
-            if (ev[k]) cudaEventDestroy(ev[k]);  // released once the work that uses them completes
-    }
+    });
     if (e != cudaSuccess) return e;
     const int smem = FDAS_RAW_CAP * (int)sizeof(unsigned long long);
     e = cudaFuncSetAttribute(fdas_hs_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -1011,6 +1019,10 @@ void harmonic_blocks(const fdas_params &p, size_t n, int *blocks_16k, int *block
 }
 
 cudaError_t prepare_harmonic_batch() {
+    // The auxiliary streams exist before any graph capture that forks into them.
+    cudaStream_t aux[2];
+    cudaError_t e = aux_streams(aux);
+    if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(fdas_hs_finalize_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 FDAS_RAW_CAP * (int)sizeof(unsigned long long));
 }
@@ -1022,6 +1034,13 @@ cudaError_t launch_harmonic_batch(const fdas_params &p, const HsBatch &B, int to
     if (e != cudaSuccess) return e;
     const int c = (p.n_temp - 1) / 2;
     const int lo1 = p.n_harm >= 2 ? c / 2 + 1 : 0;
+    struct Launch {
+        HsBatchKernel kernel;  // nullptr: fdas_hs_k1_batch
+        dim3 grid;
+        int lo;
+    };
+    Launch L[4];
+    int nl = 0;
     for (const Group &gr : kGroups) {
         int lo, hi;
         if (!group_rows(c, p.n_harm, gr.kmin, gr.kmax, &lo, &hi)) continue;
@@ -1029,18 +1048,18 @@ cudaError_t launch_harmonic_batch(const fdas_params &p, const HsBatch &B, int to
         const int rows = (lo == 0) ? 2 * hi + 1 : 2 * (hi - lo + 1);
         const int w = kChunks * kHsThreads * kl_width(kmax);
         const unsigned gx = (unsigned)(w == 16384 ? total_16k : w == 12288 ? total_12k : total_4k);
-        hs_batch_kernel(kmax)<<<dim3(gx, (unsigned)rows), kHsThreads, 0, s>>>(B, thresh, p.n_temp, p.harm_mask,
-                                                                             p.n_harm, lo);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
+        L[nl++] = {hs_batch_kernel(kmax), dim3(gx, (unsigned)rows), lo};
     }
     const int rows1 = lo1 == 0 ? 2 * c + 1 : 2 * (c - lo1 + 1);
-    if (rows1 > 0) {
-        fdas_hs_k1_batch<<<dim3((unsigned)total_4k, (unsigned)rows1), kHsThreads, 0, s>>>(B, thresh, p.n_temp,
-                                                                                        p.harm_mask, lo1);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
+    if (rows1 > 0) L[nl++] = {nullptr, dim3((unsigned)total_4k, (unsigned)rows1), lo1};
+    // Independent launches, side by side (inside a graph capture the auxiliary streams join it).
+    e = side_by_side(s, nl, true, [&](int k, cudaStream_t sk) {
+        if (L[k].kernel)
+            L[k].kernel<<<L[k].grid, kHsThreads, 0, sk>>>(B, thresh, p.n_temp, p.harm_mask, p.n_harm, L[k].lo);
+        else
+            fdas_hs_k1_batch<<<L[k].grid, kHsThreads, 0, sk>>>(B, thresh, p.n_temp, p.harm_mask, L[k].lo);
+    });
+    if (e != cudaSuccess) return e;
     fdas_hs_finalize_batch<<<dim3((unsigned)p.n_harm, (unsigned)B.count), kFinThreads,
                              FDAS_RAW_CAP * sizeof(unsigned long long), s>>>(B, p.n_temp, p.cand_cap);
     return cudaGetLastError();
