@@ -194,12 +194,17 @@ __global__ void __launch_bounds__(kThreads, 3)
         }
         if (HP1) {
             // The HP_1 peak of the item's single-plane rows: the column of this thread's best
-            // (re-read from its row), then the warp's largest key, one atomicMax per warp.
-            const unsigned loc = best_t >= 0 ? hp1_best_loc(it.plane + (size_t)best_t * it.ld + col0 + tid, best,
-                                                            best_t, col0 + tid, smask)
-                                             : 0xFFFFFFFFu;
-            const unsigned long long key = warp_peak_key_loc(best, loc);
-            if ((tid & 31) == 0 && key != 0ull) atomicMax(&hp1.peaks[0], key);
+            // (re-read from its row), then the warp's largest key, one atomicMax per warp. Peak
+            // keys only grow, so a warp whose best power is below the peak found so far skips this.
+            const unsigned wmax = __reduce_max_sync(0xFFFFFFFFu, best >= 0.0f ? __float_as_uint(best) : 0u);
+            const unsigned cur = (unsigned)(*(volatile unsigned long long *)&hp1.peaks[0] >> 32);
+            if (wmax >= cur) {  // warp-uniform
+                const unsigned loc = best_t >= 0 ? hp1_best_loc(it.plane + (size_t)best_t * it.ld + col0 + tid, best,
+                                                                best_t, col0 + tid, smask)
+                                                 : 0xFFFFFFFFu;
+                const unsigned long long key = warp_peak_key_loc(best, loc);
+                if ((tid & 31) == 0 && key != 0ull) atomicMax(&hp1.peaks[0], key);
+            }
         }
     }
 }
