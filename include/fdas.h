@@ -209,6 +209,10 @@ fdas_status fdas_convolve(const fdas_params *p, const void *d_spec, size_t n, co
  *   d_ws     workspace of at least fdas_workspace_bytes(p, n) bytes, used for counters and raw
  *            candidate keys. Its contents need no initialisation.
  * Calls that share d_ws must not overlap on the device.
+ * The kernels of one call may run side by side on two auxiliary streams that the library creates
+ * once per device (in fdas_make_templates, or at the first call that needs them) and keeps until the
+ * process exits; they are forked from and joined back into `stream` with events, so work enqueued
+ * on `stream` afterwards, and a graph captured from `stream`, see the whole harmonic sum.
  */
 fdas_status fdas_harmonic_sum(const fdas_params *p, const float *d_plane, size_t n, size_t ld,
                               const float *d_thresh, fdas_cand *d_cands, uint32_t *d_counts,

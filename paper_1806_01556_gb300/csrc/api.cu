@@ -154,6 +154,9 @@ fdas_status fdas_make_templates(const fdas_params *p, void *d_tmpl, fdas_stream_
     fdas_status st = fdas_check_params(p);
     if (st != FDAS_OK) return st;
     if (!d_tmpl || !aligned16(d_tmpl)) return FDAS_ERR_INVALID_ARG;
+    // The harmonic sum's auxiliary streams, created here so that a later graph capture of a search
+    // does not have to create them.
+    if (fdas::prepare_streams() != cudaSuccess) return FDAS_ERR_CUDA;
     return cuda_status(fdas::launch_templates(*p, d_tmpl, stream));
 }
 

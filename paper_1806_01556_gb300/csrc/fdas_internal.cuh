@@ -131,6 +131,8 @@ cudaError_t launch_harmonic(const fdas_params &p, const float *plane, size_t n, 
 fdas_status harmonic_sum_checked(const fdas_params *p, const float *d_plane, size_t n, size_t ld,
                                  const float *d_thresh, fdas_cand *d_cands, uint32_t *d_counts, fdas_cand *d_peaks,
                                  void *d_ws, size_t ws_bytes, cudaStream_t stream, bool concurrent);
+// Creates the current device's auxiliary streams of the harmonic sum if they do not exist yet.
+cudaError_t prepare_streams();
 // Batched harmonic sum: reset, one launch per group of rows over every spectrum, finalize.
 void harmonic_blocks(const fdas_params &p, size_t n, int *blocks_16k, int *blocks_12k, int *blocks_4k);
 cudaError_t prepare_harmonic_batch();

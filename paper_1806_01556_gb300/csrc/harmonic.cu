@@ -1018,10 +1018,14 @@ void harmonic_blocks(const fdas_params &p, size_t n, int *blocks_16k, int *block
     *blocks_4k = (int)((n + kK1Cols - 1) / kK1Cols);
 }
 
+cudaError_t prepare_streams() {
+    cudaStream_t aux[2];
+    return aux_streams(aux);
+}
+
 cudaError_t prepare_harmonic_batch() {
     // The auxiliary streams exist before any graph capture that forks into them.
-    cudaStream_t aux[2];
-    cudaError_t e = aux_streams(aux);
+    cudaError_t e = prepare_streams();
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(fdas_hs_finalize_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 FDAS_RAW_CAP * (int)sizeof(unsigned long long));
