@@ -899,6 +899,28 @@ cudaError_t aux_streams(cudaStream_t *out) {
 // concurrent (and two or more launches) they run side by side: k = 0 on s, k = 1 and 3 on the first
 // auxiliary stream, k = 2 on the second, forked from s and joined back into it by events, so that
 // one launch's tail overlaps the others' work. Work enqueued on s afterwards waits for all of them.
+// The fork and join events of the calling thread on the current device, created on first use and
+// reused by every later call of that thread: each call records and waits on them before it returns,
+// so no other call can see them half-way.
+cudaError_t thread_events(cudaEvent_t *ev) {
+    thread_local cudaEvent_t cache[kMaxAuxDevices][3];
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxAuxDevices) return cudaErrorInvalidDevice;
+    for (int k = 0; k < 3; ++k) {
+        if (cache[dev][k] == nullptr) {
+            e = cudaEventCreateWithFlags(&cache[dev][k], cudaEventDisableTiming);
+            if (e != cudaSuccess) {
+                cache[dev][k] = nullptr;
+                return e;
+            }
+        }
+        ev[k] = cache[dev][k];
+    }
+    return cudaSuccess;
+}
+
 template <class F>
 cudaError_t side_by_side(cudaStream_t s, int count, bool concurrent, F &&launch) {
     const bool fork = concurrent && count >= 2;
@@ -907,7 +929,7 @@ cudaError_t side_by_side(cudaStream_t s, int count, bool concurrent, F &&launch)
     cudaError_t e = cudaSuccess;
     if (fork) {
         e = aux_streams(&st[1]);
-        for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = thread_events(ev);
         if (e == cudaSuccess) e = cudaEventRecord(ev[0], s);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(st[1], ev[0], 0);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(st[2], ev[0], 0);
@@ -921,8 +943,6 @@ cudaError_t side_by_side(cudaStream_t s, int count, bool concurrent, F &&launch)
         if (e == cudaSuccess) e = cudaEventRecord(ev[2], st[2]);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[1], 0);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[2], 0);
-        for (int k = 0; k < 3; ++k)
-            if (ev[k]) cudaEventDestroy(ev[k]);  // released once the work that uses them completes
     }
     return e;
 }

@@ -435,3 +435,36 @@ def test_harmonic_highest_index_large(fd):
     got = run_harmonic(fd, p, plane, ta)
     ref = harmonic.detect(plane, ta, p.n_harm, p.harm_mask, p.cand_cap, index="highest")
     assert_same_candidates(*got, ref, p.harm_mask)
+
+
+# ---------------------------------------------------------------- graph capture of a whole search
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_search_captured_in_a_cuda_graph_equals_eager(fd, small_case, precision):
+    """fdas_search captured into a CUDA graph from a user stream (its harmonic-sum launches fork into
+    the library's auxiliary streams and join back) replays to the eager results, bit for bit."""
+    wl, _ = small_case
+    p = fd.Params(precision=precision)
+    s = fd.Searcher(p, wl.n, thresh=thresholds.threshold_array(p.n_harm, p.n_temp, sigma=3.0))
+    d_spec = torch.from_numpy(wl.spectrum).cuda()
+    s.search(d_spec, wl.n)
+    torch.cuda.synchronize()
+    want_c, want_n, want_p = s.results()
+    assert want_n.sum() > 0
+    for t in (s.cands, s.counts, s.peaks, s.plane):
+        t.zero_()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    with torch.cuda.graph(g, stream=side, capture_error_mode="thread_local"):
+        s.search(d_spec, wl.n)  # enqueued on the capturing stream
+    for _ in range(2):
+        g.replay()
+    torch.cuda.synchronize()
+    got_c, got_n, got_p = s.results()
+    assert np.array_equal(got_n, want_n)
+    for a, b in zip(got_c, want_c):
+        assert a.tobytes() == b.tobytes()
+    assert got_p.tobytes() == want_p.tobytes()
+    assert fd.fdas_device_status() == 0
