@@ -11,9 +11,9 @@
 //                    CTA. fdas_search with FP32 skips it: the convolution takes those rows' HP_1.
 //   fdas_hs_kl<KL>   the rows with at least two planes (|i| <= c/2) in three launches, by their
 //                    plane count K(i) = min(n_harm, floor(c/|i|)): 5-16, 3-4 and 2 (kGroups), each
-//                    compiled for KL terms with a per-row cap at K(i). A CTA takes 8 chunks of
-//                    256 J columns (J = 8, 6 or 2 fundamentals per thread for up to 4, 8 or 16
-//                    planes); in each chunk a thread issues every strided gather P[c + l i][l j] of
+//                    compiled for KL terms with a per-row cap at K(i). A CTA takes 16 chunks (8 in
+//                    the batched form) of 256 J columns (J = 8, 6 or 2 fundamentals per thread for
+//                    up to 4, 8 or 16 planes); in each chunk a thread issues every strided gather P[c + l i][l j] of
 //                    its J fundamentals before summing, through the read-only path, and warps whose
 //                    columns all have the same number of terms skip the per-element domain test.
 //                    Crossings are rare and take a separate path: a ballot, one atomicAdd per warp,
@@ -120,13 +120,15 @@ __device__ __forceinline__ int term_count(int j, int n) {
     return t < KL ? t : KL;
 }
 
-// Rows with KL >= 2 planes. A CTA covers kChunks chunks of 256 J fundamental columns (J = jpt<KL>()); in a
+// Rows with KL >= 2 planes. A CTA covers CH chunks of 256 J fundamental columns (J = jpt<KL>()); in a
 // chunk, lane L of warp w handles j = jc + 32 J w + L + 32 u, u < J, so every gather of a warp is one coalesced stride-l
 // access along a plane row. The per-plane best points accumulate over the chunks, and the peak
 // reductions, the block merge and the atomics run once per CTA. UNIFORM: every fundamental of the
 // warp's chunk has the same number T of terms, which holds for all warps but those straddling a
 // boundary j = (n-1)/l.
-constexpr int kChunks = 8;
+constexpr int kChunks = 8;      // batched launches (their CTA tables assume this width)
+constexpr int kChunksOne = 16;  // one spectrum: fewer, wider CTAs took the FP32 harmonic stage from 0.296
+                                // to 0.284 ms at N = 2^21 (12 chunks: 0.288, 24: 0.285, 32: 0.287)
 // Fundamentals per thread and chunk: more for few planes (more gathers in flight per thread: the
 // 2- and 4-plane launches went from 0.166 to 0.126 ms at N = 2^21 with 8 instead of 4, the 5- to
 // 8-plane launch gained 4% with 6 instead of 4), fewer for many planes, to keep the gathers in
@@ -186,7 +188,7 @@ __device__ __forceinline__ void hs_chunk(const float *const (&rp)[KL], const flo
 
 // Row i takes part in klast <= KL planes: rows with fewer planes than the kernel was compiled for cap
 // their term counts at klast (and never touch rows c + l i for l > klast).
-template <int KL>
+template <int KL, int CH>
 __device__ __forceinline__ void hs_row(const float *__restrict__ plane, int n, size_t ld, const float *__restrict__ thresh,
                                        int n_temp, unsigned mask, int c, int i, int klast, int j0,
                                        unsigned long long *raw, unsigned long long *counters,
@@ -208,7 +210,7 @@ __device__ __forceinline__ void hs_row(const float *__restrict__ plane, int n, s
         best[l] = -1.0f;
         bestj[l] = 0;
     }
-    for (int ch = 0; ch < kChunks; ++ch) {
+    for (int ch = 0; ch < CH; ++ch) {
         const int jw = j0 + ch * (kHsThreads * jpt<KL>()) + warp * (32 * jpt<KL>());
         if (jw >= n) break;  // warp-uniform
         const int t_first = min(term_count<KL>(jw, n), klast);
@@ -260,8 +262,8 @@ __global__ void __launch_bounds__(kHsThreads, KL <= 3 ? 4 : 2)
     const int i = group_row_offset(blockIdx.y, lo);
     const int ai = i < 0 ? -i : i;
     const int klast = ai == 0 ? n_harm : min(n_harm, c / ai);
-    hs_row<KL>(plane, n, ld, thresh, n_temp, mask, c, i, klast, blockIdx.x * (kChunks * kHsThreads * jpt<KL>()), raw,
-               counters, peaks);
+    hs_row<KL, kChunksOne>(plane, n, ld, thresh, n_temp, mask, c, i, klast,
+                           blockIdx.x * (kChunksOne * kHsThreads * jpt<KL>()), raw, counters, peaks);
 }
 
 // ---- highest-harmonic indexing (FDAS_INDEX_HIGHEST) ------------------------------------------------
@@ -841,7 +843,7 @@ __global__ void __launch_bounds__(kHsThreads, KL <= 3 ? 4 : 2)
     const int i = group_row_offset(blockIdx.y, lo);
     const int ai = i < 0 ? -i : i;
     const int klast = ai == 0 ? n_harm : min(n_harm, c / ai);
-    hs_row<KL>(J.plane, J.n, (size_t)J.ld, thresh, n_temp, mask, c, i, klast,
+    hs_row<KL, kChunks>(J.plane, J.n, (size_t)J.ld, thresh, n_temp, mask, c, i, klast,
                (blockIdx.x - first_block<W>(J)) * W, J.raw, J.counters,
                J.peaks);
 }
@@ -999,7 +1001,7 @@ cudaError_t launch_harmonic(const fdas_params &p, const float *plane, size_t n, 
         int lo, hi;
         if (!group_rows(c, p.n_harm, gr.kmin, gr.kmax, &lo, &hi)) continue;
         const int kmax = gr.kmax < p.n_harm ? gr.kmax : p.n_harm;
-        const int per = kChunks * kHsThreads * kl_width(kmax);
+        const int per = kChunksOne * kHsThreads * kl_width(kmax);
         const int rows = (lo == 0) ? 2 * hi + 1 : 2 * (hi - lo + 1);
         L[nl++] = {hs_kernel(kmax), dim3((unsigned)((n + per - 1) / per), (unsigned)rows), lo};
     }
