@@ -47,8 +47,8 @@ KERNEL_SOURCES = {
 NCU_TRAFFIC = {
     "convolve.cu": ("c69a1b37e08a", 669.4e6),
     "convolve_tc.cu": ("c7934a72a93f", 669.6e6),
-    "harmonic.cu": ("60995438bd5e", 1488.3e6),
-    "harmonic.cu+k1": ("60995438bd5e", 1840.9e6),
+    "harmonic.cu": ("5c1b72416b75", 1433.1e6),
+    "harmonic.cu+k1": ("5c1b72416b75", 1785.6e6),
 }
 
 
