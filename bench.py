@@ -147,6 +147,21 @@ def algorithmic(n, n_temp=85, n_tap=421, fft_len=2048, n_harm=8, rows_read=None)
     return dict(conv_flop=conv_flop, conv_bytes=conv_bytes, hs_bytes=hs_bytes, n_seg=n_seg)
 
 
+def path_roofline(n, n_tap, ms_per_step, hbm_gbs, hbm_kind, n_temp=85):
+    """The whole search against the slower of its two floors: the FFT flops at the FP32 ALU peak, and
+    the plane's bytes at the measured HBM bandwidth (written once by the convolution, read once by
+    the harmonic sum, plus the spectrum read with the segment overlap)."""
+    alg = algorithmic(n, n_temp=n_temp, n_tap=n_tap)
+    t_flop = alg["conv_flop"] / (FP32_PEAK_TFLOPS * 1e12) * 1e3
+    plane = n_temp * n * 4
+    t_bytes = (alg["conv_bytes"] + plane) / (hbm_gbs * 1e9) * 1e3
+    t_roof = max(t_flop, t_bytes)
+    return {"bound": "hbm" if t_bytes >= t_flop else "alu", "ms_at_roofline": t_roof, "ms_flop": t_flop,
+            "ms_bytes": t_bytes, "achieved_ms": ms_per_step, "frac": t_roof / ms_per_step,
+            "bytes": alg["conv_bytes"] + plane, "flop": alg["conv_flop"],
+            "peaks": f"FP32 {FP32_PEAK_TFLOPS:.1f} TFLOP/s (unit counts x clock), HBM {hbm_gbs:.0f} GB/s ({hbm_kind})"}
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 20 ms from __enter__ to __exit__.
 
@@ -469,6 +484,7 @@ def run_fdas(args):
                     "h2d_bytes_per_step": args.n * 8, "d2h_bytes_per_step": d2h},
             "gpu_launches": search_launches(head, p.n_harm, p.n_temp, args.harm_index) * args.steps,
             "roofline": roof,
+            "path_roofline": path_roofline(args.n, args.n_tap, ms_per_step, hbm, hbm_kind),
             "stages": st,
             "forms": forms,
             "cpu_baseline": cpu,
