@@ -94,3 +94,16 @@ def test_plan_graph_replay_and_tuning_keep_results(fd):
     for b in range(len(LENGTHS)):
         assert _same_written(ref[b], _written(batch, b)), b
     plan.close()
+
+
+@pytest.mark.parametrize("lengths", [[70001], [5000, 1, 90000, 300, 40000]])
+def test_batch_groupings_equal_single_spectrum_search(fd, lengths):
+    """A batch of one spectrum, and five of very uneven lengths (down to a single bin), give the same
+    results as fdas_search on each spectrum alone."""
+    p = fd.Params()
+    batch = fd.Batch(p, lengths, thresh=thresholds.threshold_array(8, 85, sigma=3.5))
+    _fill(batch, seed=8)
+    batch.search()
+    torch.cuda.synchronize()
+    for b in range(len(lengths)):
+        _same(fd, batch, b, _single(fd, batch, b))
