@@ -246,3 +246,20 @@ def test_clock_sampler_keeps_the_timed_window():
     assert s["window"] == "timed region"
     cs.t_begin, cs.t_end = t0 + 5.0, t0 + 5.01  # nothing inside: the whole run is reported
     assert cs.summary()["window"] == "whole run"
+
+
+def test_bench_path_roofline_is_the_slower_floor():
+    """bench.py's whole-path roofline: FFT flops at the FP32 peak against the plane's bytes (written
+    once, read once, plus the spectrum segments) at HBM bandwidth; the slower one bounds the step."""
+    import bench
+
+    n = 1 << 21
+    alg = bench.algorithmic(n)
+    r = bench.path_roofline(n, 421, 1.0, 6800.0, "test")
+    plane = 85 * n * 4
+    assert r["bytes"] == alg["conv_bytes"] + plane == 1289 * 2048 * 8 + 2 * plane
+    assert abs(r["ms_bytes"] - r["bytes"] / 6800e9 * 1e3) < 1e-12
+    assert abs(r["ms_flop"] - alg["conv_flop"] / (bench.FP32_PEAK_TFLOPS * 1e12) * 1e3) < 1e-12
+    assert r["bound"] == "hbm" and r["ms_at_roofline"] == r["ms_bytes"] and r["frac"] == r["ms_bytes"] / 1.0
+    fast = bench.path_roofline(n, 421, 1.0, 1e9, "test")  # absurd bandwidth: the flops bound
+    assert fast["bound"] == "alu" and fast["ms_at_roofline"] == fast["ms_flop"]
