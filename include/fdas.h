@@ -277,6 +277,19 @@ fdas_status fdas_search_host(const fdas_params *p, const void *h_spec, size_t n,
                              size_t ws_bytes, fdas_stream_t stream);
 
 /*
+ * fdas_search_host without the final wait: the copy in, the search and the copies out are enqueued
+ * on `stream` and the call returns. h_cands, h_counts and h_peaks hold the results once the stream
+ * has reached that point (cudaStreamSynchronize, or an event recorded after the call); h_spec must
+ * not change before then. With pinned host buffers and two sets of device buffers on two streams,
+ * one spectrum's copies overlap the other's search. Arguments and checks as in fdas_search_host.
+ */
+fdas_status fdas_search_host_async(const fdas_params *p, const void *h_spec, size_t n, void *d_spec,
+                                   const void *d_tmpl, float *d_plane, size_t ld, const float *d_thresh,
+                                   fdas_cand *d_cands, uint32_t *d_counts, fdas_cand *d_peaks,
+                                   fdas_cand *h_cands, uint32_t *h_counts, fdas_cand *h_peaks, void *d_ws,
+                                   size_t ws_bytes, fdas_stream_t stream);
+
+/*
  * Scratch size of fdas_harmonic_sum_noalloc: the workspace of 8 harmonic planes,
  * 8 * 8 * (FDAS_RAW_CAP + 4) bytes (about 1 MiB).
  */

@@ -36,6 +36,7 @@ __all__ = [
     "fdas_harmonic_sum",
     "fdas_search",
     "fdas_search_host",
+    "fdas_search_host_async",
     "fdas_search_convolve",
     "fdas_search_harmonic",
     "fdas_harmonic_sum_noalloc",
@@ -214,6 +215,19 @@ def fdas_search_host(p: Params, h_spec, n, d_spec, d_tmpl, d_plane, ld, d_thresh
     )
 
 
+def fdas_search_host_async(p: Params, h_spec, n, d_spec, d_tmpl, d_plane, ld, d_thresh, d_cands, d_counts, d_peaks,
+                           h_cands, h_counts, h_peaks, d_ws, ws_bytes, stream=None):
+    """fdas_search_host without the final wait: the host results are valid once `stream` gets there."""
+    _check(
+        lib().fdas_search_host_async(
+            C.byref(p.c()), _ptr(h_spec), n, _ptr(d_spec), _ptr(d_tmpl), _ptr(d_plane), ld, _ptr(d_thresh),
+            _ptr(d_cands), _ptr(d_counts), _ptr(d_peaks), _ptr(h_cands), _ptr(h_counts), _ptr(h_peaks), _ptr(d_ws),
+            ws_bytes, _stream(stream),
+        ),
+        "fdas_search_host_async",
+    )
+
+
 def fdas_harmonic_sum_noalloc(p: Params, d_plane, n, ld, d_thresh, d_cands, d_counts, d_peaks, stream=None):
     """fdas_harmonic_sum with the library's static scratch array instead of a workspace (n_harm <= 8)."""
     _check(
@@ -313,6 +327,8 @@ class Batch:
             self.peaks.append(torch.empty(params.n_harm * CAND_DTYPE.itemsize, **u8))
         with torch.cuda.device(self.device):
             fdas_make_templates(params, self.tmpl)
+            # The bank and thresholds are ready before any search, on whichever stream it runs.
+            torch.cuda.current_stream(self.device).synchronize()
 
     def entries(self):
         return [(self.specs[b], n, self.planes[b], self.ld[b], self.cands[b], self.counts[b], self.peaks[b])
@@ -435,6 +451,8 @@ class Searcher:
         self.h_peaks = torch.empty(params.n_harm * CAND_DTYPE.itemsize, dtype=torch.uint8, pin_memory=True)
         with torch.cuda.device(self.device):
             fdas_make_templates(params, self.tmpl)
+            # The bank and thresholds are ready before any search, on whichever stream it runs.
+            torch.cuda.current_stream(self.device).synchronize()
 
     def search(self, spec, n: int | None = None, stream=None) -> None:
         """Run fdas_search on a device complex64 tensor (results stay on the device)."""
@@ -448,6 +466,14 @@ class Searcher:
         fdas_search_host(self.p, h_spec, n, self.spec, self.tmpl, self.plane, self.ld, self.thresh, self.cands,
                          self.counts, self.peaks, self.h_cands, self.h_counts, self.h_peaks, self.ws, self.ws_bytes,
                          stream)
+
+    def search_host_async(self, h_spec, n: int | None = None, stream=None) -> None:
+        """fdas_search_host_async: enqueue copy in, search and copies out on `stream` and return. The
+        host results (results(host=True)) are valid once the stream has completed them."""
+        n = (h_spec.numel() if hasattr(h_spec, "numel") else h_spec.size) if n is None else n
+        fdas_search_host_async(self.p, h_spec, n, self.spec, self.tmpl, self.plane, self.ld, self.thresh, self.cands,
+                               self.counts, self.peaks, self.h_cands, self.h_counts, self.h_peaks, self.ws,
+                               self.ws_bytes, stream)
 
     def results(self, host: bool = False):
         """(per-plane candidate arrays, counts, peaks) as numpy, from the device or host buffers."""

@@ -100,6 +100,7 @@ SIGNATURES = {
     "fdas_search_convolve": (C.c_int, [P, VP, SZ, VP, VP, SZ, VP, VP, SZ, VP]),
     "fdas_search_harmonic": (C.c_int, [P, VP, SZ, SZ, VP, VP, VP, VP, VP, SZ, VP]),
     "fdas_search_host": (C.c_int, [P, VP, SZ, VP, VP, VP, SZ, VP, VP, VP, VP, VP, VP, VP, VP, SZ, VP]),
+    "fdas_search_host_async": (C.c_int, [P, VP, SZ, VP, VP, VP, SZ, VP, VP, VP, VP, VP, VP, VP, VP, SZ, VP]),
     "fdas_harmonic_sum_noalloc": (C.c_int, [P, VP, SZ, SZ, VP, VP, VP, VP, VP]),
     "fdas_batch_workspace_bytes": (SZ, [P, C.c_int]),
     "fdas_search_batch": (C.c_int, [P, VP, C.c_int, VP, VP, VP, SZ, VP, VP]),

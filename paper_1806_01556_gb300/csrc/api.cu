@@ -249,6 +249,17 @@ fdas_status fdas_search_host(const fdas_params *p, const void *h_spec, size_t n,
                              float *d_plane, size_t ld, const float *d_thresh, fdas_cand *d_cands, uint32_t *d_counts,
                              fdas_cand *d_peaks, fdas_cand *h_cands, uint32_t *h_counts, fdas_cand *h_peaks,
                              void *d_ws, size_t ws_bytes, fdas_stream_t stream) {
+    const fdas_status st = fdas_search_host_async(p, h_spec, n, d_spec, d_tmpl, d_plane, ld, d_thresh, d_cands, d_counts,
+                                                  d_peaks, h_cands, h_counts, h_peaks, d_ws, ws_bytes, stream);
+    if (st != FDAS_OK) return st;
+    return cuda_status(cudaStreamSynchronize(stream));
+}
+
+fdas_status fdas_search_host_async(const fdas_params *p, const void *h_spec, size_t n, void *d_spec,
+                                   const void *d_tmpl, float *d_plane, size_t ld, const float *d_thresh,
+                                   fdas_cand *d_cands, uint32_t *d_counts, fdas_cand *d_peaks, fdas_cand *h_cands,
+                                   uint32_t *h_counts, fdas_cand *h_peaks, void *d_ws, size_t ws_bytes,
+                                   fdas_stream_t stream) {
     fdas_status st = fdas_check_params(p);
     if (st != FDAS_OK) return st;
     if (!h_spec || !h_cands || !h_counts || (h_peaks && !d_peaks)) return FDAS_ERR_INVALID_ARG;
@@ -267,7 +278,7 @@ fdas_status fdas_search_host(const fdas_params *p, const void *h_spec, size_t n,
     if (h_peaks && (e = cudaMemcpyAsync(h_peaks, d_peaks, p->n_harm * sizeof(fdas_cand), cudaMemcpyDeviceToHost,
                                         stream)) != cudaSuccess)
         return FDAS_ERR_CUDA;
-    return cuda_status(cudaStreamSynchronize(stream));
+    return FDAS_OK;
 }
 
 }  // extern "C"

@@ -124,6 +124,10 @@ def test_bad_pointers_are_rejected_before_any_launch(fd):
     assert lib.fdas_search(C.byref(bad), fake, 100, fake, fake, 100, fake, fake, fake, null, fake, ws, null) == -2
     assert lib.fdas_search_host(C.byref(p), null, 100, fake, fake, fake, 100, fake, fake, fake, null, fake, fake,
                                 null, fake, ws, null) == -1
+    assert lib.fdas_search_host_async(C.byref(p), null, 100, fake, fake, fake, 100, fake, fake, fake, null, fake,
+                                      fake, null, fake, ws, null) == -1
+    assert lib.fdas_search_host_async(C.byref(p), fake, 100, odd, fake, fake, 100, fake, fake, fake, null, fake,
+                                      fake, null, fake, ws, null) == -1
     assert lib.fdas_default_thresholds(C.byref(p), 6.0, 2, fake) == -1
     assert lib.fdas_status_string(-3) == b"workspace too small"
     assert lib.fdas_device_status(None, 0) == -1
