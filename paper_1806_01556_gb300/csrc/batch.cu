@@ -72,9 +72,9 @@ void build_tables(const fdas_params &p, const fdas_batch_item *items, int count,
         blk1 += bk1;
         blk2 += bk2;
         const fdas::HsWorkspace ws = fdas::hs_workspace(static_cast<char *>(d_ws) + (size_t)b * stride, p.n_harm);
-        hj.counters = ws.counters;
-        hj.peaks = ws.peaks;
-        hj.raw = ws.raw;
+        hj.counters = cj.counters = ws.counters;
+        hj.peaks = cj.peaks = ws.peaks;
+        hj.raw = cj.raw = ws.raw;
         hj.cands = it.d_cands;
         hj.counts = it.d_counts;
         hj.peak_out = it.d_peaks;
@@ -106,10 +106,21 @@ cudaError_t launch_batch(const fdas_params &p, const Tables &t, const void *d_tm
     const int max_ctas = fdas::convolve_ctas_per_sm(g);  // resident CTAs per SM
     const int ctas = cfg.ctas_per_sm > 0 && cfg.ctas_per_sm < max_ctas ? cfg.ctas_per_sm : max_ctas;
     const int grid = t.conv.total_items < ctas * sms ? t.conv.total_items : ctas * sms;
-    cudaError_t e = fdas::launch_convolve_batch(g, t.conv, static_cast<const float2 *>(d_tmpl), grid,
-                                                cfg.templates_per_item, s);
+    const float2 *tmpl = static_cast<const float2 *>(d_tmpl);
+    // FP32 with fundamental indexing: the convolution takes HP_1 of the single-plane rows, as in
+    // fdas_search; the workspaces are reset before it and the harmonic sum skips those rows.
+    const bool hp1 = !conv_only && g.precision == FDAS_FP32 && p.harm_index == FDAS_INDEX_FUNDAMENTAL;
+    cudaError_t e = cudaSuccess;
+    if (hp1) {
+        e = fdas::launch_hs_reset_batch(p, t.hs, s);
+        if (e == cudaSuccess)
+            e = fdas::launch_convolve_batch_hp1(g, t.conv, tmpl, grid, cfg.templates_per_item, d_thresh, p.harm_mask,
+                                                p.n_harm, s);
+    } else {
+        e = fdas::launch_convolve_batch(g, t.conv, tmpl, grid, cfg.templates_per_item, s);
+    }
     if (e != cudaSuccess || conv_only) return e;
-    return fdas::launch_harmonic_batch(p, t.hs, t.total_16k, t.total_12k, t.total_4k, d_thresh, s);
+    return fdas::launch_harmonic_batch(p, t.hs, t.total_16k, t.total_12k, t.total_4k, d_thresh, s, hp1);
 }
 
 }  // namespace

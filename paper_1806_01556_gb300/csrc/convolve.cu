@@ -113,6 +113,12 @@ __global__ void __launch_bounds__(kThreads, 3)
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
         const Item it = jobs.get(item);
         const int n = it.n, s = it.s, t0 = it.t0, t1 = it.t1;
+        Hp1 h1 = hp1;  // HP1: a batch item's own workspace replaces the kernel's
+        if (HP1 && it.counters != nullptr) {
+            h1.raw = it.raw;
+            h1.counters = it.counters;
+            h1.peaks = it.peaks;
+        }
         const float2 *__restrict__ spec = it.spec;
         const int origin = s * keep - h;  // input index of segment point 0
         const int col0 = s * keep - h;    // column of segment time index 0
@@ -185,7 +191,7 @@ __global__ void __launch_bounds__(kThreads, 3)
             }
             if (k1row) {
                 const float ta = hp1.ta ? __ldg(&hp1.ta[t]) : __int_as_float(0x7f800000);
-                if (__any_sync(0xFFFFFFFFu, mx > ta)) hp1_emit_row(dst, ta, t, col0 + tid, smask, hp1);  // rare
+                if (__any_sync(0xFFFFFFFFu, mx > ta)) hp1_emit_row(dst, ta, t, col0 + tid, smask, h1);  // rare
                 if (mx > best) {  // strict: the first template wins ties, as in the canonical order
                     best = mx;
                     best_t = t;
@@ -197,13 +203,13 @@ __global__ void __launch_bounds__(kThreads, 3)
             // (re-read from its row), then the warp's largest key, one atomicMax per warp. Peak
             // keys only grow, so a warp whose best power is below the peak found so far skips this.
             const unsigned wmax = __reduce_max_sync(0xFFFFFFFFu, best >= 0.0f ? __float_as_uint(best) : 0u);
-            const unsigned cur = (unsigned)(*(volatile unsigned long long *)&hp1.peaks[0] >> 32);
+            const unsigned cur = (unsigned)(*(volatile unsigned long long *)&h1.peaks[0] >> 32);
             if (wmax >= cur) {  // warp-uniform
                 const unsigned loc = best_t >= 0 ? hp1_best_loc(it.plane + (size_t)best_t * it.ld + col0 + tid, best,
                                                                 best_t, col0 + tid, smask)
                                                  : 0xFFFFFFFFu;
                 const unsigned long long key = warp_peak_key_loc(best, loc);
-                if ((tid & 31) == 0 && key != 0ull) atomicMax(&hp1.peaks[0], key);
+                if ((tid & 31) == 0 && key != 0ull) atomicMax(&h1.peaks[0], key);
             }
         }
     }
@@ -320,6 +326,9 @@ cudaError_t device_status(unsigned *flags, bool clear) {
 cudaError_t prepare_convolve_batch() {
     cudaError_t e = cudaFuncSetAttribute(fdas_ols_fp32<false, BatchJobs>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(fdas_ols_fp32<true, BatchJobs>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kSmemBytes);
     if (e == cudaSuccess) e = prepare_convolve_batch_tc();
     return e;
 }
@@ -328,6 +337,20 @@ int convolve_items(const Geometry &g, size_t n, int templates_per_item) {
     int t_chunk, n_tchunk;
     chunking(g, templates_per_item, &t_chunk, &n_tchunk);
     return (int)((n + g.keep - 1) / g.keep) * n_tchunk;
+}
+
+cudaError_t launch_convolve_batch_hp1(const Geometry &g, const ConvBatch &batch, const float2 *tmpl, int grid,
+                                      int templates_per_item, const float *thresh, unsigned harm_mask, int n_harm,
+                                      cudaStream_t s) {
+    BatchJobs jobs;
+    jobs.batch = batch;
+    jobs.n_temp = g.n_temp;
+    chunking(g, templates_per_item, &jobs.t_chunk, &jobs.n_tchunk);
+    // The workspace pointers come from each item; the single-plane rows as in launch_convolve_hp1.
+    const Hp1 hp1{(harm_mask & 1u) ? thresh : nullptr, nullptr, nullptr, nullptr, g.c,
+                  n_harm >= 2 ? g.c / 2 + 1 : 0};
+    fdas_ols_fp32<true><<<grid, kThreads, kSmemBytes, s>>>(jobs, tmpl, g.n_temp, g.h, g.keep, hp1);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_convolve_batch(const Geometry &g, const ConvBatch &batch, const float2 *tmpl, int grid,

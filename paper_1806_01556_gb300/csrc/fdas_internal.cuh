@@ -59,6 +59,10 @@ struct ConvJob {
     unsigned long long ld;
     int n;
     int item0;  // first work item of this spectrum in the batch
+    // This spectrum's harmonic-sum workspace (HsWorkspace), for HP_1 taken in the convolution.
+    unsigned long long *counters;
+    unsigned long long *peaks;
+    unsigned long long *raw;
 };
 struct ConvBatch {
     int count;
@@ -121,6 +125,11 @@ cudaError_t prepare_convolve_batch();
 int convolve_items(const Geometry &g, size_t n, int templates_per_item);
 cudaError_t launch_convolve_batch(const Geometry &g, const ConvBatch &batch, const float2 *tmpl, int grid,
                                   int templates_per_item, cudaStream_t s);
+// The FP32 batched convolution that also takes HP_1 of every spectrum's single-plane rows into its
+// workspace (ConvJob counters / peaks / raw, reset beforehand).
+cudaError_t launch_convolve_batch_hp1(const Geometry &g, const ConvBatch &batch, const float2 *tmpl, int grid,
+                                      int templates_per_item, const float *thresh, unsigned harm_mask, int n_harm,
+                                      cudaStream_t s);
 // Harmonic sum. With hp1_done the workspace was reset before the convolution, which already took
 // HP_1 of the single-plane rows (launch_convolve_hp1). With concurrent the row-group launches run
 // side by side on two auxiliary streams of the library (created once per device).
@@ -136,7 +145,11 @@ cudaError_t prepare_streams();
 // Batched harmonic sum: reset, one launch per group of rows over every spectrum, finalize.
 void harmonic_blocks(const fdas_params &p, size_t n, int *blocks_16k, int *blocks_12k, int *blocks_4k);
 cudaError_t prepare_harmonic_batch();
+// hp1_done: the workspaces were reset before the convolution, which took HP_1 of the single-plane
+// rows (launch_convolve_batch_hp1); no reset and no single-plane launch run here then.
 cudaError_t launch_harmonic_batch(const fdas_params &p, const HsBatch &batch, int total_16k, int total_12k,
-                                  int total_4k, const float *thresh, cudaStream_t s);
+                                  int total_4k, const float *thresh, cudaStream_t s, bool hp1_done = false);
+// Zeroes every spectrum's counters and peak keys.
+cudaError_t launch_hs_reset_batch(const fdas_params &p, const HsBatch &batch, cudaStream_t s);
 
 }  // namespace fdas

@@ -1053,11 +1053,18 @@ cudaError_t prepare_harmonic_batch() {
                                 FDAS_RAW_CAP * (int)sizeof(unsigned long long));
 }
 
-cudaError_t launch_harmonic_batch(const fdas_params &p, const HsBatch &B, int total_16k, int total_12k, int total_4k,
-                                  const float *thresh, cudaStream_t s) {
+cudaError_t launch_hs_reset_batch(const fdas_params &p, const HsBatch &B, cudaStream_t s) {
     fdas_hs_reset_batch<<<B.count, 32, 0, s>>>(B, p.n_harm);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_harmonic_batch(const fdas_params &p, const HsBatch &B, int total_16k, int total_12k, int total_4k,
+                                  const float *thresh, cudaStream_t s, bool hp1_done) {
+    cudaError_t e = cudaSuccess;
+    if (!hp1_done) {
+        e = launch_hs_reset_batch(p, B, s);
+        if (e != cudaSuccess) return e;
+    }
     const int c = (p.n_temp - 1) / 2;
     const int lo1 = p.n_harm >= 2 ? c / 2 + 1 : 0;
     struct Launch {
@@ -1077,7 +1084,7 @@ cudaError_t launch_harmonic_batch(const fdas_params &p, const HsBatch &B, int to
         L[nl++] = {hs_batch_kernel(kmax), dim3(gx, (unsigned)rows), lo};
     }
     const int rows1 = lo1 == 0 ? 2 * c + 1 : 2 * (c - lo1 + 1);
-    if (rows1 > 0) L[nl++] = {nullptr, dim3((unsigned)total_4k, (unsigned)rows1), lo1};
+    if (rows1 > 0 && !hp1_done) L[nl++] = {nullptr, dim3((unsigned)total_4k, (unsigned)rows1), lo1};
     // Independent launches, side by side (inside a graph capture the auxiliary streams join it).
     e = side_by_side(s, nl, true, [&](int k, cudaStream_t sk) {
         if (L[k].kernel)

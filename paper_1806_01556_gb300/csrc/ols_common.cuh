@@ -187,6 +187,11 @@ struct Item {
     int s;
     int t0;
     int t1;
+    // The spectrum's harmonic-sum workspace in a batch (nullptr for a single spectrum, whose
+    // workspace the kernel gets as a parameter).
+    unsigned long long *counters;
+    unsigned long long *peaks;
+    unsigned long long *raw;
 };
 
 // Work items of a single spectrum: item = s * n_tchunk + chunk.
@@ -203,7 +208,7 @@ struct SingleJobs {
     __device__ Item get(int item) const {
         const int s = item / n_tchunk;
         const int t0 = (item - s * n_tchunk) * t_chunk;
-        return Item{spec, plane, ld, n, s, t0, min(t0 + t_chunk, n_temp)};
+        return Item{spec, plane, ld, n, s, t0, min(t0 + t_chunk, n_temp), nullptr, nullptr, nullptr};
     }
 };
 
@@ -225,7 +230,7 @@ struct BatchJobs {
         const int local = item - J.item0;
         const int s = local / n_tchunk;
         const int t0 = (local - s * n_tchunk) * t_chunk;
-        return Item{J.spec, J.plane, (size_t)J.ld, J.n, s, t0, min(t0 + t_chunk, n_temp)};
+        return Item{J.spec, J.plane, (size_t)J.ld, J.n, s, t0, min(t0 + t_chunk, n_temp), J.counters, J.peaks, J.raw};
     }
 };
 
