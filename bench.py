@@ -45,10 +45,10 @@ KERNEL_SOURCES = {
 # "harmonic.cu": the harmonic stage of an FP32 search (no single-plane launch); "harmonic.cu+k1":
 # the full harmonic sum, as the tensor-core forms run it.
 NCU_TRAFFIC = {
-    "convolve.cu": ("c69a1b37e08a", 669.4e6),
-    "convolve_tc.cu": ("c7934a72a93f", 669.6e6),
-    "harmonic.cu": ("5c1b72416b75", 1433.1e6),
-    "harmonic.cu+k1": ("5c1b72416b75", 1785.6e6),
+    "convolve.cu": ("7e3875ec313c", 669.3e6),
+    "convolve_tc.cu": ("8df7e36a91d1", 669.2e6),
+    "harmonic.cu": ("261a66b0b929", 1434.3e6),
+    "harmonic.cu+k1": ("261a66b0b929", 1786.8e6),
 }
 
 
