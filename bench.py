@@ -685,7 +685,7 @@ def run_profile(args):
     wl = synth.ska_workload(n=args.n, seed=1)
     d_spec = torch.from_numpy(wl.spectrum).cuda()
     for name in args.forms:
-        s = fdas.Searcher(fdas.Params(precision=FORMS[name], n_tap=args.n_tap), args.n)
+        s = fdas.Searcher(fdas.Params(precision=FORMS[name], n_tap=args.n_tap, harm_index=args.harm_index), args.n)
         for _ in range(args.steps):
             s.search(d_spec, args.n)
         torch.cuda.synchronize()

@@ -492,3 +492,44 @@ def test_search_host_async_on_two_streams_equals_the_synchronous_call(fd, small_
         for a, b in zip(got_c, want_c):
             assert a.tobytes() == b.tobytes()
         assert got_p.tobytes() == want_p.tobytes()
+
+
+def test_searches_from_two_host_threads_equal_one_thread(fd, small_case):
+    """Two host threads searching at the same time, each on its own searcher and stream (the
+    library's auxiliary streams are shared, its fork and join events are per thread), get the same
+    results as one thread alone."""
+    import threading
+
+    wl, _ = small_case
+    p = fd.Params()
+    ta = thresholds.threshold_array(p.n_harm, p.n_temp, sigma=3.0)
+    d_spec = torch.from_numpy(wl.spectrum).cuda()
+    ref = fd.Searcher(p, wl.n, thresh=ta)
+    ref.search(d_spec, wl.n)
+    torch.cuda.synchronize()
+    want_c, want_n, want_p = ref.results()
+    workers = [fd.Searcher(p, wl.n, thresh=ta) for _ in range(2)]
+    errors = []
+
+    def run(s):
+        try:
+            torch.cuda.set_device(0)
+            st = torch.cuda.Stream()
+            for _ in range(6):
+                s.search(d_spec, wl.n, stream=st)
+            st.synchronize()
+        except Exception as exc:  # reported below, in the test's own thread
+            errors.append(exc)
+
+    threads = [threading.Thread(target=run, args=(s,)) for s in workers]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    for s in workers:
+        got_c, got_n, got_p = s.results()
+        assert np.array_equal(got_n, want_n)
+        for a, b in zip(got_c, want_c):
+            assert a.tobytes() == b.tobytes()
+        assert got_p.tobytes() == want_p.tobytes()
