@@ -533,3 +533,59 @@ def test_searches_from_two_host_threads_equal_one_thread(fd, small_case):
         for a, b in zip(got_c, want_c):
             assert a.tobytes() == b.tobytes()
         assert got_p.tobytes() == want_p.tobytes()
+
+
+# ---------------------------------------------------------------- maximum size
+
+
+def test_search_at_the_maximum_length(fd):
+    """N = FDAS_MAX_N = 2^24 (a 5.7 GB plane), with a drifting tone near the last bin, so that
+    candidate columns use all 24 bits of the key. The oracle cannot build this plane in seconds, so
+    the check uses properties that hold at any size:
+    - sampled plane points, including the last columns, against the direct definition;
+    - every reported candidate's HP_k recomputed from the GPU plane (float32, l = 1..k) bit for
+      bit, above its threshold, in canonical order, its count at least the listed number;
+    - each plane's peak no smaller than its best candidate."""
+    n = 1 << 24
+    p = fd.Params(harm_mask=0b10001011)
+    rng = np.random.default_rng(24)
+    x = synth.complex_noise(rng, n) + synth.tone_spectrum(n, [synth.Tone(n - 3000, 5, 25.0, 1)])
+    spec = x.astype(np.complex64)
+    s = fd.Searcher(p, n)
+    s.search(torch.from_numpy(spec).cuda(), n)
+    torch.cuda.synchronize()
+    assert fd.fdas_device_status() == 0
+    cands, counts, peaks = s.results()
+    c = (p.n_temp - 1) // 2
+
+    rows = np.concatenate([rng.integers(0, 85, 24), [0, 84, 42, 47, 42, 84]])
+    cols = np.concatenate([rng.integers(0, n, 24), [n - 1, n - 1, 0, n - 3000, n - 2, 1 << 23]])
+    got = s.plane[torch.from_numpy(rows).cuda(), torch.from_numpy(cols).cuda()].cpu().numpy()
+    direct = correlate.power_at(spec, templates.template_bank(), rows, cols)
+    assert (np.abs(got - direct) / np.maximum(direct, 1.0)).max() <= REL_TOL
+
+    ta = fd.fdas_default_thresholds(p)
+    plane = s.plane
+    for k in range(1, p.n_harm + 1):
+        rec = cands[k - 1]
+        if not (p.harm_mask >> (k - 1)) & 1:
+            assert len(rec) == 0
+            continue
+        assert int(counts[k - 1]) >= len(rec)
+        keys = [(-float(r["power"]), int(r["i"]), int(r["j"])) for r in rec]
+        assert keys == sorted(keys)
+        for r in rec[:50]:
+            i, j = int(r["i"]), int(r["j"])
+            idx_r = torch.tensor([c + l * i for l in range(1, k + 1)], device="cuda")
+            idx_c = torch.tensor([l * j for l in range(1, k + 1)], device="cuda")
+            terms = plane[idx_r, idx_c].cpu().numpy().astype(np.float32)
+            hp = np.float32(terms[0])
+            for v in terms[1:]:
+                hp = np.float32(hp + v)
+            assert hp == np.float32(r["power"])
+            assert hp > ta[k - 1, c + i]
+        if len(rec):
+            assert float(peaks[k - 1]["power"]) >= float(rec[0]["power"])
+    # the tone (z = +5, mean bin n - 3000) is the loudest HP_1 point, in row +5 near its bin
+    top = cands[0][0]
+    assert int(top["i"]) == 5 and abs(int(top["j"]) - (n - 3000)) <= 2
