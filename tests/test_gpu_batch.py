@@ -107,3 +107,29 @@ def test_batch_groupings_equal_single_spectrum_search(fd, lengths):
     torch.cuda.synchronize()
     for b in range(len(lengths)):
         _same(fd, batch, b, _single(fd, batch, b))
+
+
+def test_batch_of_the_maximum_count(fd):
+    """FDAS_MAX_BATCH = 256 spectra of 1 to 5000 bins in one call (the job tables are kernel
+    parameters at their largest) and through the graph plan: a sample of spectra against
+    fdas_search alone."""
+    rng = np.random.default_rng(256)
+    lengths = [int(v) for v in rng.integers(1, 5001, 256)]
+    lengths[0], lengths[255] = 1, 5000
+    p = fd.Params(harm_mask=0b10001011)
+    batch = fd.Batch(p, lengths, thresh=thresholds.threshold_array(8, 85, sigma=3.0))
+    _fill(batch, seed=9)
+    batch.search()
+    torch.cuda.synchronize()
+    sample = [0, 1, 77, 128, 200, 255]
+    for b in sample:
+        _same(fd, batch, b, _single(fd, batch, b))
+    ref = [_written(batch, b) for b in sample]
+    plan = batch.plan()
+    for t in batch.cands + batch.planes + batch.counts + batch.peaks:
+        t.zero_()
+    plan.launch()
+    torch.cuda.synchronize()
+    for b, r in zip(sample, ref):
+        assert _same_written(r, _written(batch, b)), b
+    plan.close()
