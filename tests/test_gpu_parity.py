@@ -589,3 +589,37 @@ def test_search_at_the_maximum_length(fd):
     # the tone (z = +5, mean bin n - 3000) is the loudest HP_1 point, in row +5 near its bin
     top = cands[0][0]
     assert int(top["i"]) == 5 and abs(int(top["j"]) - (n - 3000)) <= 2
+
+
+# ---------------------------------------------------------------- largest template grid
+
+
+@pytest.fixture(scope="module")
+def grid255():
+    """255 templates (z = -127..127, the most fdas_params allows), 421 taps, N = 5000: spectrum and
+    FP64 oracle plane."""
+    grid = templates.TemplateGrid(n_temp=255, z_min=-127.0, z_step=1.0, n_tap=421)
+    bank = templates.template_bank(grid)
+    rng = np.random.default_rng(255)
+    n = 5000
+    spec = (synth.complex_noise(rng, n) + synth.tone_spectrum(n, [synth.Tone(2500, 100, 20.0, 2)])).astype(
+        np.complex64)
+    return spec, correlate.plane_ols(spec, bank, 2048)
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_largest_template_grid(fd, grid255, prec):
+    """Every convolution form on 255 templates (rows up to 254 in the candidate keys) against the
+    oracle plane, and the harmonic sum fed the oracle plane bit for bit."""
+    spec, ref = grid255
+    p = fd.Params(n_temp=255, z_min=-127, n_harm=8, harm_mask=0xFF, cand_cap=500, precision=prec)
+    got, _ = run_convolve(fd, p, spec)
+    mx, _ = plane_rel(got, ref)
+    assert mx <= REL_TOL
+    if prec == 0:
+        plane32 = ref.astype(np.float32)
+        ta = thresholds.threshold_array(8, 255, sigma=3.5)
+        res = run_harmonic(fd, p, plane32, ta)
+        want = harmonic.detect(plane32, ta, 8, 0xFF, 500)
+        assert sum(want.counts) > 0
+        assert_same_candidates(*res, want, 0xFF)
