@@ -30,7 +30,8 @@ N_DEFAULT = 1 << 21
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
-# FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 flop (FMA) x 2.07 GHz.
+# Nominal FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 flop (FMA) x 2.07 GHz. Reported beside the
+# measured one (fdas_measure_fp32_peak, FFMA chains on every SM), which is the roofline denominator.
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the last ncu capture of
@@ -147,19 +148,20 @@ def algorithmic(n, n_temp=85, n_tap=421, fft_len=2048, n_harm=8, rows_read=None)
     return dict(conv_flop=conv_flop, conv_bytes=conv_bytes, hs_bytes=hs_bytes, n_seg=n_seg)
 
 
-def path_roofline(n, n_tap, ms_per_step, hbm_gbs, hbm_kind, n_temp=85):
+def path_roofline(n, n_tap, ms_per_step, hbm_gbs, hbm_kind, n_temp=85, fp32_tflops=FP32_PEAK_TFLOPS,
+                  fp32_kind="unit counts x clock"):
     """The whole search against the slower of its two floors: the FFT flops at the FP32 ALU peak, and
     the plane's bytes at the measured HBM bandwidth (written once by the convolution, read once by
     the harmonic sum, plus the spectrum read with the segment overlap)."""
     alg = algorithmic(n, n_temp=n_temp, n_tap=n_tap)
-    t_flop = alg["conv_flop"] / (FP32_PEAK_TFLOPS * 1e12) * 1e3
+    t_flop = alg["conv_flop"] / (fp32_tflops * 1e12) * 1e3
     plane = n_temp * n * 4
     t_bytes = (alg["conv_bytes"] + plane) / (hbm_gbs * 1e9) * 1e3
     t_roof = max(t_flop, t_bytes)
     return {"bound": "hbm" if t_bytes >= t_flop else "alu", "ms_at_roofline": t_roof, "ms_flop": t_flop,
             "ms_bytes": t_bytes, "achieved_ms": ms_per_step, "frac": t_roof / ms_per_step,
             "bytes": alg["conv_bytes"] + plane, "flop": alg["conv_flop"],
-            "peaks": f"FP32 {FP32_PEAK_TFLOPS:.1f} TFLOP/s (unit counts x clock), HBM {hbm_gbs:.0f} GB/s ({hbm_kind})"}
+            "peaks": f"FP32 {fp32_tflops:.1f} TFLOP/s ({fp32_kind}), HBM {hbm_gbs:.0f} GB/s ({hbm_kind})"}
 
 
 class ClockSampler:
@@ -280,56 +282,170 @@ def job_throughput(world: int, steps: int, seconds: float) -> float:
     return world * steps / seconds
 
 
-def cpu_oracle_sample(wl, sample_bins):
-    """Time the FP64 oracle (overlap-save plane + Algorithm 1) on the first sample_bins bins.
+# ---- the FP64 oracle on the host's cores (CPU baseline and reference arm) ---------------------------
+# The oracle's plane_ols runs unmodified on contiguous column blocks of the spectrum, one block per
+# task, in a pool of worker processes (one per core). Column j of the plane depends only on bins
+# j-h..j+h, so a block [j0, j1) is computed from bins [j0-h, j1+h) (clipped to the spectrum, where the
+# zero padding is the oracle's own) and its columns [j0, j1) are exact. The workers write float32 rows
+# into shared memory; the main process then runs the oracle's Algorithm 1 (harmonic.detect) on the
+# whole plane, single-threaded, as it stands.
+_W = {}
 
-    Returns (seconds per full spectrum, description). The oracle's template bank is built before
-    timing: templates are fixed per parameter set, as on the device.
-    """
-    from oracle import correlate, harmonic, templates, thresholds
 
-    bank = templates.template_bank()
-    ta = thresholds.threshold_array(8, 85)
-    x = wl.spectrum[:sample_bins]
-    t0 = time.perf_counter()
-    plane = correlate.plane_ols(x, bank, 2048)
-    harmonic.detect(plane.astype(np.float32), ta, 8, 0xFF, 200)
-    dt = time.perf_counter() - t0
-    scale = wl.n / sample_bins
-    desc = (f"oracle plane_ols + harmonic.detect on the first {sample_bins} of {wl.n} bins "
-            f"(85 templates, 8 planes), x{scale:g} to one spectrum; numpy, 1 thread")
-    return dt * scale, desc
+def _oracle_worker_init(spec_name, plane_name, n, n_temp, bank, h, fft_len):
+    from multiprocessing import shared_memory
+
+    _W["shm"] = [shared_memory.SharedMemory(name=spec_name), shared_memory.SharedMemory(name=plane_name)]
+    _W["spec"] = np.ndarray((n,), dtype=np.complex128, buffer=_W["shm"][0].buf)
+    _W["plane"] = np.ndarray((n_temp, n), dtype=np.float32, buffer=_W["shm"][1].buf)
+    _W["bank"], _W["h"], _W["fft_len"] = bank, h, fft_len
+
+
+def _oracle_block(task):
+    from oracle import correlate
+
+    j0, j1, n = task
+    h = _W["h"]
+    a, b = max(0, j0 - h), min(n, j1 + h)
+    p = correlate.plane_ols(_W["spec"][a:b], _W["bank"], _W["fft_len"])
+    _W["plane"][:, j0:j1] = p[:, j0 - a : j1 - a]
+    return j1 - j0
+
+
+class OraclePool:
+    """The oracle's plane (all host cores) and harmonic sum for spectra of up to n_max bins."""
+
+    def __init__(self, n_max, n_temp=85, n_tap=421, fft_len=2048, workers=None):
+        import multiprocessing as mp
+        from multiprocessing import shared_memory
+
+        from oracle import templates, thresholds
+
+        self.cores = workers or len(os.sched_getaffinity(0))
+        self.n_max, self.n_temp, self.fft_len = n_max, n_temp, fft_len
+        grid = templates.TemplateGrid(n_temp=n_temp, z_min=-float((n_temp - 1) // 2), z_step=1.0, n_tap=n_tap)
+        self.bank = templates.template_bank(grid)
+        self.ta = thresholds.threshold_array(8, n_temp)
+        self._shm = [shared_memory.SharedMemory(create=True, size=n_max * 16),
+                     shared_memory.SharedMemory(create=True, size=n_temp * n_max * 4)]
+        self.spec = np.ndarray((n_max,), dtype=np.complex128, buffer=self._shm[0].buf)
+        # spawn: the workers start clean, whatever CUDA state this process has or will have
+        ctx = mp.get_context("spawn")
+        env = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        for k in env:
+            os.environ[k] = "1"
+        try:
+            self.pool = ctx.Pool(self.cores, initializer=_oracle_worker_init,
+                                 initargs=(self._shm[0].name, self._shm[1].name, n_max, n_temp, self.bank,
+                                           (n_tap - 1) // 2, fft_len))
+        finally:
+            for k, v in env.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        self.pool.map(_oracle_block, [(0, 1, 1)] * self.cores)  # every worker imported the oracle
+
+    def run(self, spectrum):
+        """One search of `spectrum` (its first n bins): seconds for the plane and for Algorithm 1."""
+        from oracle import harmonic
+
+        n = len(spectrum)
+        self.spec[:n] = spectrum
+        self.spec[n:] = 0
+        blocks = 4 * self.cores
+        edges = np.linspace(0, n, blocks + 1).astype(np.int64)
+        tasks = [(int(a), int(b), n) for a, b in zip(edges[:-1], edges[1:]) if b > a]
+        t0 = time.perf_counter()
+        self.pool.map(_oracle_block, tasks, chunksize=1)
+        t1 = time.perf_counter()
+        plane = np.ndarray((self.n_temp, self.n_max), dtype=np.float32, buffer=self._shm[1].buf)
+        res = harmonic.detect(np.ascontiguousarray(plane[:, :n]) if n < self.n_max else plane, self.ta, 8, 0xFF,
+                              200)
+        t2 = time.perf_counter()
+        return t1 - t0, t2 - t1, res
+
+    def close(self):
+        self.pool.terminate()
+        self.pool.join()
+        self.spec = None
+        for m in self._shm:
+            m.close()
+            m.unlink()
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def cpu_baseline(wl, runs=3):
+    """The oracle on one whole spectrum on all host cores, median of `runs` (spectra/s)."""
+    pool = OraclePool(wl.n)
+    try:
+        times = [pool.run(wl.spectrum)[:2] for _ in range(runs)]
+    finally:
+        pool.close()
+    tot = [a + b for a, b in times]
+    med = float(np.median(tot))
+    return {"value": 1.0 / med, "unit": "spectra/s", "cores": pool.cores, "kind": "oracle",
+            "cpu": cpu_model(), "median_of": runs, "s_per_spectrum": med,
+            "s_plane": float(np.median([a for a, _ in times])), "s_harmonic": float(np.median([b for _, b in times])),
+            "sample": f"the whole spectrum ({wl.n} bins, 85 templates, 8 planes): oracle plane_ols on "
+                      f"{pool.cores} worker processes over column blocks, then harmonic.detect (1 thread)"}
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle, as it stands, on the host's cores (rank 0 only). Each step
+    searches the whole spectrum, unless the run has more than 40 steps in all, in which case each
+    step searches a contiguous sample of ~N*40/(steps+warmup) bins, so that the run stays within
+    about two minutes; value is spectra/s either way and ms_per_step the measured time of a step."""
     world, rank, _ = dist_env()
     if rank != 0:
         return
     import synth
 
     wl = synth.ska_workload(n=args.n, seed=1)
-    sample = min(args.n, 1 << 16)
-    for _ in range(args.warmup):
-        cpu_oracle_sample(wl, sample)
-    times = []
-    desc = ""
-    for _ in range(args.steps):
-        t, desc = cpu_oracle_sample(wl, sample)
-        times.append(t)
+    total = args.steps + args.warmup
+    bins = wl.n if total <= 40 else max(1 << 16, int(wl.n * 40 / total))
+    pool = OraclePool(bins)
+    try:
+        for _ in range(args.warmup):
+            pool.run(wl.spectrum[:bins])
+        times = []
+        for _ in range(args.steps):
+            a, b, _ = pool.run(wl.spectrum[:bins])
+            times.append(a + b)
+    finally:
+        pool.close()
     sec = float(np.mean(times))
-    value = 1.0 / sec
+    frac = bins / wl.n
+    value = frac / sec
+    sample = (f"{'the whole spectrum' if bins == wl.n else f'the first {bins} of {wl.n} bins'} per step "
+              f"({frac:g} spectrum), 85 templates, 8 planes: oracle plane_ols on {pool.cores} worker processes "
+              "over column blocks, then harmonic.detect (1 thread)")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "spectra/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(args.n),
-        "cpu_baseline": {"value": value, "unit": "spectra/s", "cores": 1, "kind": "oracle", "sample": desc},
+        "config": workload_config(args.n, args.n_tap, args.harm_index, "fp32"),
+        "spectra_per_step": frac,
+        "cpu_baseline": {"value": value, "unit": "spectra/s", "cores": pool.cores, "kind": "oracle",
+                         "cpu": cpu_model(), "sample": sample},
         "e2e": {"value": value, "unit": "spectra/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def workload_config(n, n_tap=421):
+def workload_config(n, n_tap=421, harm_index=0, precision="fp32"):
+    """The workload both arms report. precision is the convolution form in value (the reference arm
+    computes in FP64 and reports the FP32 form it stands beside)."""
     return {
         "workload": f"SKA-sized spectrum N={n} (2^{int(np.log2(n))}), 4 drifting tones x 8 harmonics in unit "
                     f"complex Gaussian noise (seed 1, rank r uses seed 1+r); 85 templates z=-42..42, {n_tap} taps, "
@@ -337,6 +453,8 @@ def workload_config(n, n_tap=421):
         "n": n, "n_temp": 85, "n_tap": n_tap, "fft_len": 2048, "n_harm": 8,
         "l2": "inputs larger than L2: the 713 MB plane is written and read every step",
         "parallelism": "replicas (one spectrum per GPU, no collective)",
+        "harm_index": "highest" if harm_index else "fundamental",
+        "precision": precision,
     }
 
 
@@ -360,8 +478,7 @@ def run_fdas(args):
     # The CPU baseline runs before any timed GPU work (rank 0, N = 1 only).
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        sec, desc = cpu_oracle_sample(wl, min(args.n, 1 << 19))
-        cpu = {"value": 1.0 / sec, "unit": "spectra/s", "cores": 1, "kind": "oracle", "sample": desc}
+        cpu = cpu_baseline(wl)
 
     d_spec = torch.from_numpy(wl.spectrum).to(dev)
     stream = torch.cuda.current_stream(dev)
@@ -410,6 +527,19 @@ def run_fdas(args):
                 "conv_ms": float(np.mean([e[0].elapsed_time(e[1]) for e in events])),
                 "hs_ms": float(np.mean([e[1].elapsed_time(e[2]) for e in events]))}
 
+    # The FP32 CUDA-core peak of this GPU, measured (FFMA chains on every SM for about 200 ms), with the
+    # clocks it ran at: the denominator of the FP32 convolution's roofline.
+    fp32_sampler = ClockSampler(local)
+    with fp32_sampler:
+        fp32_sampler.begin()
+        fp32_tflops, fp32_ms = fdas.fdas_measure_fp32_peak(200.0)
+        fp32_sampler.end()
+    fp32_peak = {"value": fp32_tflops, "unit": "TFLOP/s", "timed_ms": fp32_ms, "clocks": fp32_sampler.summary(),
+                 "nominal": FP32_PEAK_TFLOPS,
+                 "how": "fdas_measure_fp32_peak: 8 independent FFMA chains per thread, 4 CTAs of 256 threads per "
+                        "SM, 2 flop per FFMA, CUDA events"}
+    fp32_src = "measured (fdas_measure_fp32_peak, FFMA chains on every SM)"
+
     # The form that goes in "value" is timed with the clock sampler; the others are timed the same way.
     results, samplers = {}, {}
     for name, s in searchers.items():
@@ -420,6 +550,23 @@ def run_fdas(args):
     p = s.p
     ms_per_step = results[head]["total_ms"] / args.steps
     value = job_throughput(world, args.steps, results[head]["total_ms"] / 1e3)
+
+    # A longer run of the same steps (about one second, untimed for value) for a fuller clock record
+    # under load, with its own per-step time as a consistency check.
+    soak_sampler = ClockSampler(local)
+    soak_steps = max(args.steps, int(1000.0 / max(ms_per_step, 1e-3)))
+    with soak_sampler:
+        barrier()
+        torch.cuda.synchronize(dev)
+        soak_sampler.begin()
+        sa, sb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        sa.record(stream)
+        for _ in range(soak_steps):
+            step(s)
+        sb.record(stream)
+        torch.cuda.synchronize(dev)
+        soak_sampler.end()
+    soak = {"steps": soak_steps, "ms_per_step": sa.elapsed_time(sb) / soak_steps, "clocks": soak_sampler.summary()}
 
     # A stream of spectra: the plain convolution and the full harmonic sum of each spectrum, spectra
     # alternating over two streams and planes, so that one spectrum's harmonic sum (HBM-bound) runs
@@ -495,8 +642,8 @@ def run_fdas(args):
             conv_tflops = alg["conv_flop"] / conv_s / 1e12
             hs_gbs = alg["hs_bytes"] / hs_s / 1e9
             conv = {"ms": r["conv_ms"], "bound": "alu", "achieved": conv_tflops, "unit": "TFLOP/s",
-                    "peak": FP32_PEAK_TFLOPS, "frac": conv_tflops / FP32_PEAK_TFLOPS,
-                    "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                    "peak": fp32_tflops, "frac": conv_tflops / fp32_tflops, "peak_source": fp32_src,
+                    "frac_of_nominal": conv_tflops / FP32_PEAK_TFLOPS,
                     "hbm_gbs": alg["conv_bytes"] / conv_s / 1e9,
                     "traffic": traffic_for("convolve.cu" if name == "fp32" else "convolve_tc.cu")}
             if name != "fp32":
@@ -524,9 +671,7 @@ def run_fdas(args):
         roof = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
                 "frac": d["frac"], "traffic": d["traffic"], "peak_source": d["peak_source"]}
         d2h = p.n_harm * p.cand_cap * 12 + p.n_harm * 4 + p.n_harm * 12
-        cfg = workload_config(args.n, args.n_tap)
-        cfg["harm_index"] = "highest" if args.harm_index else "fundamental"
-        cfg["precision"] = head
+        cfg = workload_config(args.n, args.n_tap, args.harm_index, head)
         line = {
             "metric": METRIC, "value": value, "unit": "spectra/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -539,7 +684,10 @@ def run_fdas(args):
                     "one_call_at_a_time": job_throughput(world, args.steps, e2e_sync_s)},
             "gpu_launches": search_launches(head, p.n_harm, p.n_temp, args.harm_index) * args.steps,
             "roofline": roof,
-            "path_roofline": path_roofline(args.n, args.n_tap, ms_per_step, hbm, hbm_kind),
+            "path_roofline": path_roofline(args.n, args.n_tap, ms_per_step, hbm, hbm_kind, fp32_tflops=fp32_tflops,
+                                           fp32_kind="measured"),
+            "fp32_peak": fp32_peak,
+            "clocks_soak": soak,
             "stages": st,
             "forms": forms,
             "cpu_baseline": cpu,

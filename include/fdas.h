@@ -40,6 +40,7 @@ typedef int fdas_status;
 #define FDAS_ERR_UNSUPPORTED (-2) /* valid parameters this build has no kernel for             */
 #define FDAS_ERR_WORKSPACE (-3)   /* workspace smaller than fdas_workspace_bytes()             */
 #define FDAS_ERR_CUDA (-4)        /* a CUDA runtime call or kernel launch failed               */
+#define FDAS_ERR_TIMEOUT (-5)     /* a kernel gave up on a bounded device wait: outputs invalid */
 
 /* Arithmetic of the FT convolution: plain FP32 FFTs, or part of each inverse DFT as a GEMM on the
  * tensor cores with 16-bit operands split in two (BF16 halves, or FP16 halves with scaling). */
@@ -121,9 +122,28 @@ const char *fdas_status_string(fdas_status s);
  * counterpart: its kernels run on an FPGA without such waits.
  *   *flags receives the bits (OR over every launch since the last clear); clear != 0 zeroes them.
  *   The read is synchronous with respect to the device (it waits for earlier work on the legacy
- *   default stream). Returns FDAS_ERR_INVALID_ARG for a null flags, FDAS_ERR_CUDA if the read fails. */
+ *   default stream). Returns FDAS_ERR_INVALID_ARG for a null flags, FDAS_ERR_CUDA if the read fails.
+ * How a timeout reaches the caller: an asynchronous call returns before its kernels run, so it
+ * cannot return what they find later; the caller reads this word after synchronising. The calls
+ * that wait on the device themselves read it before they return, and report FDAS_ERR_TIMEOUT when
+ * FDAS_DEV_WAIT_TIMEOUT is set: fdas_search_host, fdas_batch_plan_tune, and the request loop's
+ * per-request fdas_result.status. They leave the word as it is (clear it with this call). */
 #define FDAS_DEV_WAIT_TIMEOUT 1u
 fdas_status fdas_device_status(uint32_t *flags, int clear);
+
+/* Sets the device status word of the current device to flags (synchronously, like
+ * fdas_device_status). A diagnostic with no counterpart in the paper: it lets a program test its
+ * handling of FDAS_ERR_TIMEOUT without making any kernel wait run out. Returns FDAS_ERR_CUDA if the
+ * write fails. */
+fdas_status fdas_set_device_status(uint32_t flags);
+
+/* Measures the FP32 CUDA-core peak of the current device: a kernel of independent FFMA chains on
+ * every SM (each FFMA counts 2 flop) runs for about `ms` milliseconds (10..2000), timed with CUDA
+ * events. *tflops receives the rate in TFLOP/s and *elapsed_ms the timed duration. A diagnostic with
+ * no counterpart in the paper: it is the denominator of the FP32 convolution's roofline.
+ * Synchronous. Returns FDAS_ERR_INVALID_ARG for null outputs or ms out of range, FDAS_ERR_CUDA if a
+ * CUDA call fails. */
+fdas_status fdas_measure_fp32_peak(float ms, double *tflops, float *elapsed_ms);
 
 /* Diagnostic of the bounded-wait path; no counterpart in the paper. Runs, on the current device,
  * one thread that waits on an mbarrier nothing completes, through the same bounded wait the
@@ -209,10 +229,15 @@ fdas_status fdas_convolve(const fdas_params *p, const void *d_spec, size_t n, co
  *   d_ws     workspace of at least fdas_workspace_bytes(p, n) bytes, used for counters and raw
  *            candidate keys. Its contents need no initialisation.
  * Calls that share d_ws must not overlap on the device.
- * The kernels of one call may run side by side on two auxiliary streams that the library creates
- * once per device (in fdas_make_templates, or at the first call that needs them) and keeps until the
- * process exits; they are forked from and joined back into `stream` with events, so work enqueued
- * on `stream` afterwards, and a graph captured from `stream`, see the whole harmonic sum.
+ * The kernels of one call may run side by side on two auxiliary streams of the library, forked from
+ * and joined back into `stream` with events, so work enqueued on `stream` afterwards, and a graph
+ * captured from `stream`, see the whole harmonic sum. There is one pair per host thread, CUDA
+ * context and caller stream (up to 8 pairs per thread, the least recently used pair going to a new
+ * caller stream), made at the first call that needs it or in fdas_make_templates on that stream, and
+ * kept until the process exits. So calls from other threads, or on other streams, never share these
+ * streams, and a capture in one thread records none of another thread's work. No pair is made while
+ * `stream` is being captured: a captured call on a stream that has none runs its kernels on `stream`
+ * alone, with the same results. A pair made before cudaDeviceReset is never used afterwards.
  */
 fdas_status fdas_harmonic_sum(const fdas_params *p, const float *d_plane, size_t n, size_t ld,
                               const float *d_thresh, fdas_cand *d_cands, uint32_t *d_counts,
@@ -253,7 +278,9 @@ fdas_status fdas_search(const fdas_params *p, const void *d_spec, size_t n, cons
  * It copies h_spec (complex64[n], pinned memory recommended) into d_spec, runs fdas_search,
  * copies the candidates, counts and (if h_peaks is not NULL) peaks back to the host, and waits
  * for the stream. d_cands, d_counts and d_peaks are device staging buffers of the same shapes as
- * in fdas_harmonic_sum (d_peaks may be NULL only if h_peaks is NULL).
+ * in fdas_harmonic_sum (d_peaks may be NULL only if h_peaks is NULL). Returns FDAS_ERR_TIMEOUT if,
+ * once the stream is done, the device status word shows that a kernel gave up on a bounded wait
+ * (fdas_device_status); the results are not valid then.
  */
 /*
  * The two stages of fdas_search, for callers that time or schedule them apart. Arguments as in
@@ -302,13 +329,20 @@ fdas_status fdas_search_host_async(const fdas_params *p, const void *h_spec, siz
  * loop that must never call cudaMalloc (which can synchronise the whole device).
  *
  * The scratch is a static device array of FDAS_NOALLOC_SCRATCH_BYTES inside libfdas. Every GPU
- * that loads the library holds it until the process exits. The call allocates nothing: no
- * cudaMalloc, no cudaFree, no allocating library routine. Arguments and results are as for
- * fdas_harmonic_sum, which it calls with that array as d_ws.
+ * that loads the library's device code holds it until the process exits. The call allocates
+ * nothing: no cudaMalloc, no cudaFree, no allocating library routine. Arguments and results are as
+ * for fdas_harmonic_sum, which it calls with that array as d_ws, on `stream` alone (no auxiliary
+ * streams).
  *   - Parameter sets whose workspace exceeds the array (n_harm > 8) are rejected with
  *     FDAS_ERR_WORKSPACE, before anything is enqueued.
  *   - The first call on a device looks up the array's device address, with that device current.
- *     Make that first call before any stream capture.
+ *     With CUDA's lazy module loading (the default), that lookup is also what loads the array into
+ *     the device's memory: the driver reserves its FDAS_NOALLOC_SCRATCH_BYTES then. Later calls
+ *     reserve nothing. Make that first call before any stream capture, and before measuring free
+ *     memory if the figure matters.
+ *   - cudaDeviceReset destroys the array with the context. The next call on that device (in the new
+ *     context) loads it again and looks up its new address; the address cached for the old context is
+ *     never used again.
  *   - All calls on a device share the one array, which keeps the last call's contents. Each call
  *     clears the counters it needs before use. Calls that overlap on the GPU (on different
  *     streams, or from different host threads) race on the array and must be serialised by the
@@ -352,13 +386,25 @@ fdas_status fdas_search_batch(const fdas_params *p, const fdas_batch_item *items
                               fdas_stream_t stream);
 
 /*
+ * fdas_harmonic_sum on count (1..FDAS_MAX_BATCH) planes of any lengths, with the batched kernels of
+ * fdas_search_batch: one launch per group of rows over every plane, then one finalize launch
+ * (Sec. 2.2, Algorithm 1, as in fdas_harmonic_sum). Each item's d_plane (n_temp x ld floats) is
+ * read; its d_spec is not used and may be NULL. Results are those of fdas_harmonic_sum on each plane
+ * alone, bit for bit. d_ws holds fdas_batch_workspace_bytes(p, count) bytes. Enqueues kernels only.
+ */
+fdas_status fdas_harmonic_sum_batch(const fdas_params *p, const fdas_batch_item *items, int count,
+                                    const float *d_thresh, void *d_ws, size_t ws_bytes, fdas_stream_t stream);
+
+/*
  * A batch plan: fdas_search_batch with fixed buffers, replayed as a CUDA graph.
  *   create  checks and copies the item list (the buffers themselves are not copied and must stay valid).
  *   tune    times the candidate convolution launch shapes (ctas_per_sm in {0, 2}, templates_per_item in
  *           {0, 43, 29, 17}) on the plan's own spectra with CUDA events, keeps the fastest, and returns
- *           it with its convolution time per batch. It waits on stream.
+ *           it with its convolution time per batch. It waits on stream, and returns FDAS_ERR_TIMEOUT
+ *           (keeping the previous shape) if a timed kernel gave up on a bounded wait.
  *   launch  enqueues the batch on stream. The first launch (and the first after tune) captures the
- *           launches into a CUDA graph on a private stream; later launches replay that graph.
+ *           launches into a CUDA graph on the plan's private stream (a thread-local capture: other
+ *           threads may run searches meanwhile); later launches replay that graph.
  *   destroy frees the plan and its graph.
  * A plan holds host memory and a CUDA graph; it allocates no device memory.
  */
@@ -376,7 +422,8 @@ void fdas_batch_plan_destroy(fdas_batch_plan *plan);
 typedef struct {
     uint64_t id;                       /* the caller's request id */
     uint64_t n;                        /* spectrum length */
-    fdas_status status;                /* FDAS_OK, or the error of this request */
+    fdas_status status;                /* FDAS_OK, or the error of this request (FDAS_ERR_TIMEOUT: the
+                                          device status showed a bounded wait that gave up) */
     int32_t pad;
     double submit_s;                   /* fdas_server_submit returned */
     double admit_s;                    /* the request got a slot and its device memory, and was launched */

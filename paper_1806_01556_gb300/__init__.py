@@ -26,6 +26,8 @@ __all__ = [
     "fdas_check_params",
     "fdas_device_status",
     "fdas_check_wait_timeout",
+    "fdas_set_device_status",
+    "fdas_measure_fp32_peak",
     "fdas_templates_bytes",
     "fdas_plane_bytes",
     "fdas_workspace_bytes",
@@ -44,6 +46,7 @@ __all__ = [
     "Searcher",
     "fdas_batch_workspace_bytes",
     "fdas_search_batch",
+    "fdas_harmonic_sum_batch",
     "BatchPlan",
     "Batch",
     "Server",
@@ -114,6 +117,18 @@ def fdas_device_status(clear: bool = False) -> int:
     flags = C.c_uint32(0)
     _check(lib().fdas_device_status(C.byref(flags), int(clear)), "fdas_device_status")
     return flags.value
+
+
+def fdas_set_device_status(flags: int) -> None:
+    """Sets the current device's status word (a diagnostic for testing FDAS_ERR_TIMEOUT handling)."""
+    _check(lib().fdas_set_device_status(flags), "fdas_set_device_status")
+
+
+def fdas_measure_fp32_peak(ms: float = 50.0) -> tuple[float, float]:
+    """FFMA-chain FP32 throughput of the current device: (TFLOP/s, timed milliseconds)."""
+    tf, el = C.c_double(), C.c_float()
+    _check(lib().fdas_measure_fp32_peak(ms, C.byref(tf), C.byref(el)), "fdas_measure_fp32_peak")
+    return tf.value, el.value
 
 
 def fdas_check_wait_timeout() -> int:
@@ -263,6 +278,16 @@ def fdas_search_batch(p: Params, entries, d_tmpl, d_thresh, d_ws, ws_bytes, ctas
     )
 
 
+def fdas_harmonic_sum_batch(p: Params, entries, d_thresh, d_ws, ws_bytes, stream=None) -> None:
+    """Harmonic sum of every entry's plane (the d_spec of an entry may be None)."""
+    arr = _items(entries)
+    _check(
+        lib().fdas_harmonic_sum_batch(C.byref(p.c()), C.cast(arr, C.c_void_p), len(entries), _ptr(d_thresh),
+                                      _ptr(d_ws), ws_bytes, _stream(stream)),
+        "fdas_harmonic_sum_batch",
+    )
+
+
 class BatchPlan:
     """fdas_batch_plan: a batch with fixed buffers, replayed as a CUDA graph; tune() picks the launch shape."""
 
@@ -337,6 +362,10 @@ class Batch:
     def search(self, ctas_per_sm=0, templates_per_item=0, stream=None) -> None:
         fdas_search_batch(self.p, self.entries(), self.tmpl, self.thresh, self.ws, self.ws_bytes, ctas_per_sm,
                           templates_per_item, stream)
+
+    def harmonic_sum(self, stream=None) -> None:
+        """fdas_harmonic_sum_batch on the batch's planes as they stand (e.g. planes written by the caller)."""
+        fdas_harmonic_sum_batch(self.p, self.entries(), self.thresh, self.ws, self.ws_bytes, stream)
 
     def plan(self) -> BatchPlan:
         return BatchPlan(self.p, self.entries(), self.tmpl, self.thresh, self.ws, self.ws_bytes)

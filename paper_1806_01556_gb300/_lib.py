@@ -16,6 +16,7 @@ FDAS_ERR_INVALID_ARG = -1
 FDAS_ERR_UNSUPPORTED = -2
 FDAS_ERR_WORKSPACE = -3
 FDAS_ERR_CUDA = -4
+FDAS_ERR_TIMEOUT = -5
 FDAS_DEV_WAIT_TIMEOUT = 1
 
 FDAS_FP32, FDAS_BF16X3, FDAS_FP16S = 0, 1, 2
@@ -87,6 +88,8 @@ SIGNATURES = {
     "fdas_check_params": (C.c_int, [P]),
     "fdas_status_string": (C.c_char_p, [C.c_int]),
     "fdas_device_status": (C.c_int, [C.POINTER(C.c_uint32), C.c_int]),
+    "fdas_set_device_status": (C.c_int, [C.c_uint32]),
+    "fdas_measure_fp32_peak": (C.c_int, [C.c_float, C.POINTER(C.c_double), C.POINTER(C.c_float)]),
     "fdas_check_wait_timeout": (C.c_int, [C.POINTER(C.c_uint32)]),
     "fdas_templates_bytes": (SZ, [P]),
     "fdas_plane_bytes": (SZ, [P, SZ, SZ]),
@@ -104,6 +107,7 @@ SIGNATURES = {
     "fdas_harmonic_sum_noalloc": (C.c_int, [P, VP, SZ, SZ, VP, VP, VP, VP, VP]),
     "fdas_batch_workspace_bytes": (SZ, [P, C.c_int]),
     "fdas_search_batch": (C.c_int, [P, VP, C.c_int, VP, VP, VP, SZ, VP, VP]),
+    "fdas_harmonic_sum_batch": (C.c_int, [P, VP, C.c_int, VP, VP, SZ, VP]),
     "fdas_batch_plan_create": (C.c_int, [P, VP, C.c_int, VP, VP, VP, SZ, C.POINTER(C.c_void_p)]),
     "fdas_batch_plan_tune": (C.c_int, [VP, VP, VP, C.POINTER(C.c_float)]),
     "fdas_batch_plan_launch": (C.c_int, [VP, VP]),

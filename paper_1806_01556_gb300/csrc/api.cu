@@ -1,7 +1,10 @@
 // C ABI entry points of libfdas: argument checks, workspace carving and kernel launches.
 // Declarations and the full contract of each call are in include/fdas.h.
+#include <cuda.h>  // driver API types only; the entry points are looked up through the runtime
+
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "fdas_internal.cuh"
 
@@ -44,6 +47,39 @@ double gamma_threshold(int k, double p) {
 }
 
 }  // namespace
+
+cudaError_t fdas::current_context_id(unsigned long long *id) {
+    // cuCtxGetCurrent and cuCtxGetId from the driver, through the runtime (no link to libcuda).
+    using GetCurrent = CUresult (*)(CUcontext *);
+    using GetId = CUresult (*)(CUcontext, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static cudaError_t init = cudaErrorUnknown;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+        void *f1 = nullptr, *f2 = nullptr;
+        init = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1);
+        if (init == cudaSuccess) init = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+        if (init == cudaSuccess && (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2))
+            init = cudaErrorNotSupported;
+        get_current = reinterpret_cast<GetCurrent>(f1);
+        get_id = reinterpret_cast<GetId>(f2);
+    });
+    if (init != cudaSuccess) return init;
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS) return cudaErrorUnknown;
+    if (ctx == nullptr) {
+        // No context is current on this thread yet: cudaSetDevice makes the device's primary context
+        // current (and creates it if needed).
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaSetDevice(dev);
+        if (e != cudaSuccess) return e;
+        if (get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr) return cudaErrorUnknown;
+    }
+    return get_id(ctx, id) == CUDA_SUCCESS ? cudaSuccess : cudaErrorUnknown;
+}
 
 fdas_status fdas::harmonic_sum_checked(const fdas_params *p, const float *d_plane, size_t n, size_t ld,
                                        const float *d_thresh, fdas_cand *d_cands, uint32_t *d_counts,
@@ -102,6 +138,7 @@ const char *fdas_status_string(fdas_status s) {
         case FDAS_ERR_UNSUPPORTED: return "unsupported parameters";
         case FDAS_ERR_WORKSPACE: return "workspace too small";
         case FDAS_ERR_CUDA: return "CUDA error";
+        case FDAS_ERR_TIMEOUT: return "a kernel gave up on a bounded device wait";
         default: return "unknown status";
     }
 }
@@ -112,6 +149,15 @@ fdas_status fdas_device_status(uint32_t *flags, int clear) {
     if (fdas::device_status(&v, clear != 0) != cudaSuccess) return FDAS_ERR_CUDA;
     *flags = v;
     return FDAS_OK;
+}
+
+fdas_status fdas_set_device_status(uint32_t flags) {
+    return fdas::set_device_status(flags) == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
+}
+
+fdas_status fdas_measure_fp32_peak(float ms, double *tflops, float *elapsed_ms) {
+    if (!tflops || !elapsed_ms || !(ms >= 10.0f) || ms > 2000.0f) return FDAS_ERR_INVALID_ARG;
+    return fdas::measure_fp32_peak(ms, tflops, elapsed_ms) == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
 }
 
 fdas_status fdas_check_wait_timeout(uint32_t *flags) {
@@ -154,9 +200,9 @@ fdas_status fdas_make_templates(const fdas_params *p, void *d_tmpl, fdas_stream_
     fdas_status st = fdas_check_params(p);
     if (st != FDAS_OK) return st;
     if (!d_tmpl || !aligned16(d_tmpl)) return FDAS_ERR_INVALID_ARG;
-    // The harmonic sum's auxiliary streams, created here so that a later graph capture of a search
-    // does not have to create them.
-    if (fdas::prepare_streams() != cudaSuccess) return FDAS_ERR_CUDA;
+    // The harmonic sum's auxiliary streams for this thread and stream, made here so that a later
+    // graph capture of a search on the same stream finds them.
+    if (fdas::prepare_streams(stream) != cudaSuccess) return FDAS_ERR_CUDA;
     return cuda_status(fdas::launch_templates(*p, d_tmpl, stream));
 }
 
@@ -252,7 +298,12 @@ fdas_status fdas_search_host(const fdas_params *p, const void *h_spec, size_t n,
     const fdas_status st = fdas_search_host_async(p, h_spec, n, d_spec, d_tmpl, d_plane, ld, d_thresh, d_cands, d_counts,
                                                   d_peaks, h_cands, h_counts, h_peaks, d_ws, ws_bytes, stream);
     if (st != FDAS_OK) return st;
-    return cuda_status(cudaStreamSynchronize(stream));
+    // The device status words, read on the same stream behind the search.
+    unsigned flags[2] = {0u, 0u};
+    cudaError_t e = fdas::device_status_async(flags, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return FDAS_ERR_CUDA;
+    return ((flags[0] | flags[1]) & FDAS_DEV_WAIT_TIMEOUT) ? FDAS_ERR_TIMEOUT : FDAS_OK;
 }
 
 fdas_status fdas_search_host_async(const fdas_params *p, const void *h_spec, size_t n, void *d_spec,

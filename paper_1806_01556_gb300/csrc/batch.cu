@@ -16,20 +16,23 @@ bool aligned(const void *p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p
 
 size_t hs_ws_stride(const fdas_params &p) { return (fdas::hs_workspace_words(p.n_harm) * 8u + 255u) / 256u * 256u; }
 
+// with_spec: the items' spectra and the template bank are used (a search); without, only the planes
+// are read (a harmonic sum).
 fdas_status check_items(const fdas_params *p, const fdas_batch_item *items, int count, const void *d_tmpl,
-                        const float *d_thresh, void *d_ws, size_t ws_bytes) {
+                        const float *d_thresh, void *d_ws, size_t ws_bytes, bool with_spec = true) {
     fdas_status st = fdas_check_params(p);
     if (st != FDAS_OK) return st;
     if (p->harm_index != FDAS_INDEX_FUNDAMENTAL) return FDAS_ERR_UNSUPPORTED;  // the batched launches index by fundamental
-    if (!items || count < 1 || count > FDAS_MAX_BATCH || !d_tmpl || !d_thresh || !d_ws) return FDAS_ERR_INVALID_ARG;
-    if (!aligned(d_tmpl, 16) || !aligned(d_ws, 16) || !aligned(d_thresh, 4)) return FDAS_ERR_INVALID_ARG;
+    if (!items || count < 1 || count > FDAS_MAX_BATCH || !d_thresh || !d_ws) return FDAS_ERR_INVALID_ARG;
+    if (with_spec && (!d_tmpl || !aligned(d_tmpl, 16))) return FDAS_ERR_INVALID_ARG;
+    if (!aligned(d_ws, 16) || !aligned(d_thresh, 4)) return FDAS_ERR_INVALID_ARG;
     if (ws_bytes < fdas_batch_workspace_bytes(p, count)) return FDAS_ERR_WORKSPACE;
     for (int b = 0; b < count; ++b) {
         const fdas_batch_item &it = items[b];
         if (it.n < 1 || it.n > FDAS_MAX_N || it.ld < it.n) return FDAS_ERR_INVALID_ARG;
-        if (!it.d_spec || !it.d_plane || !it.d_cands || !it.d_counts) return FDAS_ERR_INVALID_ARG;
-        if (!aligned(it.d_spec, 16) || !aligned(it.d_plane, 16) || !aligned(it.d_cands, 4) || !aligned(it.d_counts, 4) ||
-            !aligned(it.d_peaks, 4))
+        if (!it.d_plane || !it.d_cands || !it.d_counts) return FDAS_ERR_INVALID_ARG;
+        if (with_spec && (!it.d_spec || !aligned(it.d_spec, 16))) return FDAS_ERR_INVALID_ARG;
+        if (!aligned(it.d_plane, 16) || !aligned(it.d_cands, 4) || !aligned(it.d_counts, 4) || !aligned(it.d_peaks, 4))
             return FDAS_ERR_INVALID_ARG;
     }
     return FDAS_OK;
@@ -135,6 +138,8 @@ struct fdas_batch_plan {
     fdas_launch_config cfg;
     fdas_batch_item items[FDAS_MAX_BATCH];
     Tables tables;
+    cudaStream_t cap;  // private stream the graph is captured on (its auxiliary streams are made
+                       // before each capture begins)
     cudaGraph_t graph;
     cudaGraphExec_t exec;
 };
@@ -164,6 +169,20 @@ fdas_status fdas_search_batch(const fdas_params *p, const fdas_batch_item *items
     return e == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
 }
 
+fdas_status fdas_harmonic_sum_batch(const fdas_params *p, const fdas_batch_item *items, int count,
+                                    const float *d_thresh, void *d_ws, size_t ws_bytes, fdas_stream_t stream) {
+    fdas_status st = check_items(p, items, count, nullptr, d_thresh, d_ws, ws_bytes, false);
+    if (st != FDAS_OK) return st;
+    Tables *t = new (std::nothrow) Tables;
+    if (!t) return FDAS_ERR_INVALID_ARG;
+    build_tables(*p, items, count, d_ws, 0, t);
+    cudaError_t e = fdas::prepare_harmonic_batch();
+    if (e == cudaSuccess)
+        e = fdas::launch_harmonic_batch(*p, t->hs, t->total_16k, t->total_12k, t->total_4k, d_thresh, stream, false);
+    delete t;
+    return e == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
+}
+
 fdas_status fdas_batch_plan_create(const fdas_params *p, const fdas_batch_item *items, int count, const void *d_tmpl,
                                    const float *d_thresh, void *d_ws, size_t ws_bytes, fdas_batch_plan **out) {
     if (!out) return FDAS_ERR_INVALID_ARG;
@@ -179,7 +198,8 @@ fdas_status fdas_batch_plan_create(const fdas_params *p, const fdas_batch_item *
     plan->d_ws = d_ws;
     plan->count = count;
     std::memcpy(plan->items, items, sizeof(fdas_batch_item) * (size_t)count);
-    if (sm_count(&plan->sms) != cudaSuccess || prepare() != cudaSuccess) {
+    if (sm_count(&plan->sms) != cudaSuccess || prepare() != cudaSuccess ||
+        cudaStreamCreateWithFlags(&plan->cap, cudaStreamNonBlocking) != cudaSuccess) {
         delete plan;
         return FDAS_ERR_CUDA;
     }
@@ -198,9 +218,12 @@ static void drop_graph(fdas_batch_plan *plan) {
 fdas_status fdas_batch_plan_launch(fdas_batch_plan *plan, fdas_stream_t stream) {
     if (!plan) return FDAS_ERR_INVALID_ARG;
     if (!plan->exec) {
-        // Capture the batch once on a private stream, then replay it on the caller's streams.
-        cudaStream_t cap = nullptr;
-        cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        // Capture the batch once on the plan's private stream, then replay it on the caller's
+        // streams. The capture is thread-local, and the auxiliary streams it forks into belong to
+        // this thread and this private stream, so searches that other threads run meanwhile neither
+        // join the graph nor break the capture.
+        cudaStream_t cap = plan->cap;
+        cudaError_t e = fdas::prepare_streams(cap);
         if (e != cudaSuccess) return FDAS_ERR_CUDA;
         e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
@@ -210,7 +233,6 @@ fdas_status fdas_batch_plan_launch(fdas_batch_plan *plan, fdas_stream_t stream) 
             if (le != cudaSuccess) e = le;
         }
         if (e == cudaSuccess) e = cudaGraphInstantiate(&plan->exec, plan->graph, 0);
-        cudaStreamDestroy(cap);
         if (e != cudaSuccess) {
             drop_graph(plan);
             return FDAS_ERR_CUDA;
@@ -253,6 +275,12 @@ fdas_status fdas_batch_plan_tune(fdas_batch_plan *plan, fdas_stream_t stream, fd
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     if (e != cudaSuccess) return FDAS_ERR_CUDA;
+    // The timed launches have finished: a kernel that gave up on a bounded wait shows in the status.
+    unsigned flags[2] = {0u, 0u};
+    e = fdas::device_status_async(flags, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return FDAS_ERR_CUDA;
+    if ((flags[0] | flags[1]) & FDAS_DEV_WAIT_TIMEOUT) return FDAS_ERR_TIMEOUT;
     plan->cfg = best;
     build_tables(plan->p, plan->items, plan->count, plan->d_ws, best.templates_per_item, &plan->tables);
     drop_graph(plan);  // the next launch captures the new shape
@@ -264,6 +292,7 @@ fdas_status fdas_batch_plan_tune(fdas_batch_plan *plan, fdas_stream_t stream, fd
 void fdas_batch_plan_destroy(fdas_batch_plan *plan) {
     if (!plan) return;
     drop_graph(plan);
+    if (plan->cap) cudaStreamDestroy(plan->cap);
     delete plan;
 }
 

@@ -323,6 +323,20 @@ cudaError_t device_status(unsigned *flags, bool clear) {
     return e;
 }
 
+cudaError_t device_status_async(unsigned *h_flags2, cudaStream_t s) {
+    cudaError_t e = cudaMemcpyFromSymbolAsync(&h_flags2[0], g_device_status, sizeof(unsigned), 0,
+                                              cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = device_status_tc_async(&h_flags2[1], s);
+    return e;
+}
+
+cudaError_t set_device_status(unsigned flags) {
+    cudaError_t e = cudaMemcpyToSymbol(g_device_status, &flags, sizeof(unsigned));
+    unsigned tc = 0u;
+    if (e == cudaSuccess) e = device_status_tc(&tc, true);  // one word holds the new state
+    return e;
+}
+
 cudaError_t prepare_convolve_batch() {
     cudaError_t e = cudaFuncSetAttribute(fdas_ols_fp32<false, BatchJobs>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);

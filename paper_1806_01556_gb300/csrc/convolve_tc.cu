@@ -468,4 +468,8 @@ cudaError_t device_status_tc(unsigned *flags, bool clear) {
     return e;
 }
 
+cudaError_t device_status_tc_async(unsigned *h_flags, cudaStream_t s) {
+    return cudaMemcpyFromSymbolAsync(h_flags, g_device_status, sizeof(unsigned), 0, cudaMemcpyDeviceToHost, s);
+}
+
 }  // namespace fdas

@@ -106,6 +106,7 @@ cudaError_t prepare_convolve_batch_tc();
 cudaError_t launch_convolve_batch_tc(const Geometry &g, const ConvBatch &batch, const float2 *tmpl, int grid,
                                      int templates_per_item, cudaStream_t s);
 cudaError_t device_status_tc(unsigned *flags, bool clear);
+cudaError_t device_status_tc_async(unsigned *h_flags, cudaStream_t s);
 // Resident CTAs per SM of the convolution kernel for g.precision.
 inline int convolve_ctas_per_sm(const Geometry &g) { return g.precision == FDAS_FP32 ? 3 : kTcMaxCtasPerSm; }
 // Zeroes the harmonic-sum workspace's counters and peak keys.
@@ -118,6 +119,13 @@ cudaError_t launch_convolve_hp1(const Geometry &g, const float2 *spec, size_t n,
                                 cudaStream_t s);
 // Status bits set by kernels on the device (bit 0: a bounded wait timed out); optionally cleared.
 cudaError_t device_status(unsigned *flags, bool clear);
+// Enqueues on s copies of the two translation units' status words into h_flags2[0] and h_flags2[1]
+// (valid once s reaches them; with pageable host memory the call itself waits for that).
+cudaError_t device_status_async(unsigned *h_flags2, cudaStream_t s);
+// Sets the status word to flags (the tensor-core unit's word is cleared).
+cudaError_t set_device_status(unsigned flags);
+// FP32 FFMA-chain throughput of the current device over about ms milliseconds (diag.cu).
+cudaError_t measure_fp32_peak(float ms, double *tflops, float *elapsed_ms);
 // Runs a kernel whose bounded wait must give up; returns the status bits it left (then cleared).
 cudaError_t check_wait_timeout(unsigned *flags);
 // Batched convolution: one persistent launch over every segment of every spectrum.
@@ -132,7 +140,8 @@ cudaError_t launch_convolve_batch_hp1(const Geometry &g, const ConvBatch &batch,
                                       cudaStream_t s);
 // Harmonic sum. With hp1_done the workspace was reset before the convolution, which already took
 // HP_1 of the single-plane rows (launch_convolve_hp1). With concurrent the row-group launches run
-// side by side on two auxiliary streams of the library (created once per device).
+// side by side on two auxiliary streams of the library (one pair per host thread, context and caller
+// stream).
 cudaError_t launch_harmonic(const fdas_params &p, const float *plane, size_t n, size_t ld,
                             const float *thresh, fdas_cand *cands, uint32_t *counts, fdas_cand *peaks,
                             const HsWorkspace &ws, cudaStream_t s, bool hp1_done = false, bool concurrent = true);
@@ -140,8 +149,13 @@ cudaError_t launch_harmonic(const fdas_params &p, const float *plane, size_t n, 
 fdas_status harmonic_sum_checked(const fdas_params *p, const float *d_plane, size_t n, size_t ld,
                                  const float *d_thresh, fdas_cand *d_cands, uint32_t *d_counts, fdas_cand *d_peaks,
                                  void *d_ws, size_t ws_bytes, cudaStream_t stream, bool concurrent);
-// Creates the current device's auxiliary streams of the harmonic sum if they do not exist yet.
-cudaError_t prepare_streams();
+// Creates the calling thread's auxiliary streams of the harmonic sum for caller stream s on the
+// current context, unless they exist or s is being captured.
+cudaError_t prepare_streams(cudaStream_t s);
+// The driver's id of the current device's context (made current if it is not), unique for the life
+// of the process: caches keyed by it never hand out a resource of a context that cudaDeviceReset
+// destroyed.
+cudaError_t current_context_id(unsigned long long *id);
 // Batched harmonic sum: reset, one launch per group of rows over every spectrum, finalize.
 void harmonic_blocks(const fdas_params &p, size_t n, int *blocks_16k, int *blocks_12k, int *blocks_4k);
 cudaError_t prepare_harmonic_batch();

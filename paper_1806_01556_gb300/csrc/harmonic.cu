@@ -28,7 +28,6 @@
 //   fdas_hs_finalize one CTA per plane. A bitonic sort of the raw keys (2, 4 or 16 keys per thread in
 //                    registers, shuffles for the middle strides, shared memory for the largest), then
 //                    the top cand_cap keys decoded into fdas_cand records, the counts and the peaks.
-#include <mutex>
 #include <type_traits>
 
 #include "hs_keys.cuh"
@@ -872,28 +871,102 @@ cudaError_t launch_hs_reset(const fdas_params &p, const HsWorkspace &ws, cudaStr
     return cudaGetLastError();
 }
 
-// Two auxiliary streams per device for the concurrent row-group launches, created on first use and
-// kept for the life of the process.
-constexpr int kMaxAuxDevices = 128;
-std::mutex g_aux_mutex;
-cudaStream_t g_aux[kMaxAuxDevices][2];
+// Auxiliary streams for the concurrent row-group launches, with the fork and join events of a call.
+// There is one set per host thread, CUDA context and caller stream, so that:
+//   - calls from different threads never share a stream or an event, and a graph capture in one
+//     thread cannot pick up another thread's kernels;
+//   - calls on different caller streams of one thread (the request loop's slots) do not queue
+//     behind one another on the auxiliary streams;
+//   - a set made for a context that was destroyed (cudaDeviceReset) is never used again: the key
+//     holds the driver's context id, which is unique for the life of the process.
+// A thread keeps at most kAuxSets sets. When they are all taken, the least recently used set of the
+// current context is handed to the new caller stream, unless its streams are part of a capture in
+// progress; a set of another context is forgotten instead (its handles are not touched). Sets are
+// never created while the caller's stream is being captured: such a call runs its launches on the
+// caller's stream alone (same results, no overlap). Streams and events are kept until the process
+// exits.
+constexpr int kAuxSets = 8;
+struct AuxSet {
+    unsigned long long ctx;   // driver context id
+    unsigned long long sid;   // caller stream id (cudaStreamGetId)
+    unsigned long long used;  // last use, in this thread's call count
+    cudaStream_t st[2];
+    cudaEvent_t ev[3];
+};
 
-cudaError_t aux_streams(cudaStream_t *out) {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxAuxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_aux_mutex);
-    for (int k = 0; k < 2; ++k) {
-        if (g_aux[dev][k] == nullptr) {
-            e = cudaStreamCreateWithFlags(&g_aux[dev][k], cudaStreamNonBlocking);
-            if (e != cudaSuccess) {
-                g_aux[dev][k] = nullptr;
-                return e;
-            }
-        }
-        out[k] = g_aux[dev][k];
+bool stream_capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone;
+}
+
+cudaError_t make_aux(AuxSet &a) {
+    a.st[0] = a.st[1] = nullptr;
+    a.ev[0] = a.ev[1] = a.ev[2] = nullptr;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaStreamCreateWithFlags(&a.st[k], cudaStreamNonBlocking);
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&a.ev[k], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        for (int k = 0; k < 2; ++k)
+            if (a.st[k]) cudaStreamDestroy(a.st[k]);
+        for (int k = 0; k < 3; ++k)
+            if (a.ev[k]) cudaEventDestroy(a.ev[k]);
+        a.st[0] = nullptr;
     }
+    return e;
+}
+
+// The calling thread's set for stream s on the current context, or *out = nullptr when the launches
+// must stay on s (s is being captured and has no set yet, or every set is held by a capture).
+cudaError_t aux_set(cudaStream_t s, AuxSet **out) {
+    thread_local AuxSet sets[kAuxSets];
+    thread_local unsigned long long calls = 0;
+    *out = nullptr;
+    unsigned long long ctx = 0, sid = 0;
+    cudaError_t e = current_context_id(&ctx);
+    if (e == cudaSuccess) e = cudaStreamGetId(s, &sid);
+    if (e != cudaSuccess) return e;
+    ++calls;
+    AuxSet *hit = nullptr, *empty = nullptr, *other = nullptr, *lru = nullptr;
+    for (AuxSet &a : sets) {
+        if (a.st[0] == nullptr) {
+            if (!empty) empty = &a;
+        } else if (a.ctx != ctx) {
+            if (!other) other = &a;
+        } else if (a.sid == sid) {
+            hit = &a;
+        } else if (!lru || a.used < lru->used) {
+            lru = &a;
+        }
+    }
+    if (hit) {
+        hit->used = calls;
+        *out = hit;
+        return cudaSuccess;
+    }
+    if (stream_capturing(s)) return cudaSuccess;  // create nothing inside a capture
+    AuxSet *slot = empty ? empty : other;
+    if (slot) {
+        e = make_aux(*slot);
+        if (e != cudaSuccess) return e;
+    } else {
+        // Reuse the least recently used set of this context whose streams no capture holds.
+        for (int tries = 0; tries < kAuxSets && lru; ++tries) {
+            if (!stream_capturing(lru->st[0]) && !stream_capturing(lru->st[1])) {
+                slot = lru;
+                break;
+            }
+            AuxSet *next = nullptr;
+            for (AuxSet &a : sets)
+                if (a.st[0] && a.ctx == ctx && a.sid != sid && a.used > lru->used && (!next || a.used < next->used))
+                    next = &a;
+            lru = next;
+        }
+        if (!slot) return cudaSuccess;
+    }
+    slot->ctx = ctx;
+    slot->sid = sid;
+    slot->used = calls;
+    *out = slot;
     return cudaSuccess;
 }
 
@@ -901,50 +974,31 @@ cudaError_t aux_streams(cudaStream_t *out) {
 // concurrent (and two or more launches) they run side by side: k = 0 on s, k = 1 and 3 on the first
 // auxiliary stream, k = 2 on the second, forked from s and joined back into it by events, so that
 // one launch's tail overlaps the others' work. Work enqueued on s afterwards waits for all of them.
-// The fork and join events of the calling thread on the current device, created on first use and
-// reused by every later call of that thread: each call records and waits on them before it returns,
-// so no other call can see them half-way.
-cudaError_t thread_events(cudaEvent_t *ev) {
-    thread_local cudaEvent_t cache[kMaxAuxDevices][3];
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxAuxDevices) return cudaErrorInvalidDevice;
-    for (int k = 0; k < 3; ++k) {
-        if (cache[dev][k] == nullptr) {
-            e = cudaEventCreateWithFlags(&cache[dev][k], cudaEventDisableTiming);
-            if (e != cudaSuccess) {
-                cache[dev][k] = nullptr;
-                return e;
-            }
-        }
-        ev[k] = cache[dev][k];
-    }
-    return cudaSuccess;
-}
-
+// Each call records and waits on its set's events before it returns, so no other call sees them
+// half-way.
 template <class F>
 cudaError_t side_by_side(cudaStream_t s, int count, bool concurrent, F &&launch) {
-    const bool fork = concurrent && count >= 2;
-    cudaStream_t st[3] = {s, s, s};
-    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    AuxSet *aux = nullptr;
     cudaError_t e = cudaSuccess;
+    if (concurrent && count >= 2) e = aux_set(s, &aux);
+    const bool fork = aux != nullptr;
+    cudaStream_t st[3] = {s, s, s};
     if (fork) {
-        e = aux_streams(&st[1]);
-        if (e == cudaSuccess) e = thread_events(ev);
-        if (e == cudaSuccess) e = cudaEventRecord(ev[0], s);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(st[1], ev[0], 0);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(st[2], ev[0], 0);
+        st[1] = aux->st[0];
+        st[2] = aux->st[1];
+        e = cudaEventRecord(aux->ev[0], s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st[1], aux->ev[0], 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st[2], aux->ev[0], 0);
     }
     for (int k = 0; k < count && e == cudaSuccess; ++k) {
         launch(k, fork ? st[k == 0 ? 0 : (k & 1) ? 1 : 2] : s);
         e = cudaGetLastError();
     }
     if (fork) {
-        if (e == cudaSuccess) e = cudaEventRecord(ev[1], st[1]);
-        if (e == cudaSuccess) e = cudaEventRecord(ev[2], st[2]);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[1], 0);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[2], 0);
+        if (e == cudaSuccess) e = cudaEventRecord(aux->ev[1], st[1]);
+        if (e == cudaSuccess) e = cudaEventRecord(aux->ev[2], st[2]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, aux->ev[1], 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, aux->ev[2], 0);
     }
     return e;
 }
@@ -1040,15 +1094,12 @@ void harmonic_blocks(const fdas_params &p, size_t n, int *blocks_16k, int *block
     *blocks_4k = (int)((n + kK1Cols - 1) / kK1Cols);
 }
 
-cudaError_t prepare_streams() {
-    cudaStream_t aux[2];
-    return aux_streams(aux);
+cudaError_t prepare_streams(cudaStream_t s) {
+    AuxSet *aux = nullptr;
+    return aux_set(s, &aux);
 }
 
 cudaError_t prepare_harmonic_batch() {
-    // The auxiliary streams exist before any graph capture that forks into them.
-    cudaError_t e = prepare_streams();
-    if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(fdas_hs_finalize_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 FDAS_RAW_CAP * (int)sizeof(unsigned long long));
 }
@@ -1085,7 +1136,8 @@ cudaError_t launch_harmonic_batch(const fdas_params &p, const HsBatch &B, int to
     }
     const int rows1 = lo1 == 0 ? 2 * c + 1 : 2 * (c - lo1 + 1);
     if (rows1 > 0 && !hp1_done) L[nl++] = {nullptr, dim3((unsigned)total_4k, (unsigned)rows1), lo1};
-    // Independent launches, side by side (inside a graph capture the auxiliary streams join it).
+    // Independent launches, side by side (inside a graph capture the stream's auxiliary streams join
+    // it, if they were made before the capture began).
     e = side_by_side(s, nl, true, [&](int k, cudaStream_t sk) {
         if (L[k].kernel)
             L[k].kernel<<<L[k].grid, kHsThreads, 0, sk>>>(B, thresh, p.n_temp, p.harm_mask, p.n_harm, L[k].lo);

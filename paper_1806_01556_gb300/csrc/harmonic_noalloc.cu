@@ -1,8 +1,10 @@
 // fdas_harmonic_sum_noalloc: the harmonic-sum entry point for callers that cannot allocate
 // device memory. Its scratch (crossing counters, per-plane peak keys and raw candidate keys)
 // lives in one file-scope device array instead of a caller-provided workspace. The array is
-// sized for up to 8 harmonic planes (the paper's N_hp) and is held by every GPU that loads
-// the library until the process exits.
+// sized for up to 8 harmonic planes (the paper's N_hp). The CUDA driver loads it into a device's
+// memory when the library's code is first loaded there (with lazy module loading, the default, that
+// is the first call of this entry point on that device, inside its address lookup), and it stays
+// until the process exits or the context is reset.
 #include <mutex>
 
 #include "fdas_internal.cuh"
@@ -16,24 +18,33 @@ static_assert(FDAS_NOALLOC_SCRATCH_BYTES % sizeof(unsigned long long) == 0, "scr
 static __device__ __align__(256) unsigned long long g_fdas_noalloc_scratch[kNoallocWords];
 
 constexpr int kMaxDevices = 128;
-void *g_scratch_addr[kMaxDevices];  // device address of the array, per device ordinal
+struct ScratchAddr {
+    unsigned long long ctx;  // driver context id the address belongs to (0: none yet)
+    void *addr;              // device address of the array in that context
+};
+ScratchAddr g_scratch_addr[kMaxDevices];  // per device ordinal
 std::mutex g_scratch_mutex;
 
 // In host code g_fdas_noalloc_scratch is only a host-side stand-in for the device array, so its
-// device address is looked up once per device, with that device current.
+// device address is looked up once per device, with that device current. The address belongs to the
+// device's context: after cudaDeviceReset the device gets a new context (with a new id), in which the
+// array is loaded again, so the address is looked up again then.
 cudaError_t scratch_address(void **out) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    unsigned long long ctx = 0;
+    e = fdas::current_context_id(&ctx);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    if (g_scratch_addr[dev] == nullptr) {
+    if (g_scratch_addr[dev].addr == nullptr || g_scratch_addr[dev].ctx != ctx) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_fdas_noalloc_scratch);
         if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = p;
+        g_scratch_addr[dev] = ScratchAddr{ctx, p};
     }
-    *out = g_scratch_addr[dev];
+    *out = g_scratch_addr[dev].addr;
     return cudaSuccess;
 }
 

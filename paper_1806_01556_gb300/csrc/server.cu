@@ -118,6 +118,7 @@ struct fdas_server {
     Arena *arena = nullptr;
     std::vector<Slot> slots;
     size_t cand_bytes = 0;
+    size_t status_off = 0;  // offset of the two device status words in a slot's staging buffer
     std::mutex mu;
     std::condition_variable cv;
     std::deque<Request> pending;
@@ -151,6 +152,7 @@ static fdas_status launch_request(fdas_server *sv, Slot &s, const Footprint &f) 
             cudaSuccess ||
         cudaMemcpyAsync(s.h_stage + sv->cand_bytes + nh * 4, base + f.peaks, nh * sizeof(fdas_cand),
                         cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        fdas::device_status_async(reinterpret_cast<unsigned *>(s.h_stage + sv->status_off), st) != cudaSuccess ||
         cudaEventRecord(s.done, st) != cudaSuccess)
         return FDAS_ERR_CUDA;
     return FDAS_OK;
@@ -202,6 +204,13 @@ bool fdas_server::complete_one(Slot &s) {
     res.admit_s = s.admit_s;
     res.done_s = now_s();
     if (s.status == FDAS_OK) {
+        // The device status words, copied behind this request's search: a kernel that gave up on a
+        // bounded wait since the last clear makes the result invalid.
+        unsigned flags[2];
+        std::memcpy(flags, s.h_stage + status_off, sizeof(flags));
+        if ((flags[0] | flags[1]) & FDAS_DEV_WAIT_TIMEOUT) res.status = FDAS_ERR_TIMEOUT;
+    }
+    if (res.status == FDAS_OK) {
         const size_t nh = (size_t)p.n_harm;
         std::memcpy(res.counts, s.h_stage + cand_bytes, nh * 4);
         std::memcpy(res.peaks, s.h_stage + cand_bytes + nh * 4, nh * sizeof(fdas_cand));
@@ -255,7 +264,8 @@ fdas_status fdas_server_create(const fdas_params *p, size_t device_bytes, int ma
     if (e == cudaSuccess && fdas_make_templates(p, sv->d_tmpl, nullptr) != FDAS_OK) e = cudaErrorLaunchFailure;
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     sv->slots.resize((size_t)max_inflight);
-    const size_t stage = sv->cand_bytes + (size_t)p->n_harm * (4 + sizeof(fdas_cand));
+    sv->status_off = (sv->cand_bytes + (size_t)p->n_harm * (4 + sizeof(fdas_cand)) + 7) / 8 * 8;
+    const size_t stage = sv->status_off + 2 * sizeof(unsigned);
     for (auto &s : sv->slots) {
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);

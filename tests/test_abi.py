@@ -25,7 +25,7 @@ def fd():
 def declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(fdas_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(fdas_[a-z0-9_]+)\s*\(", text)))
 
 
 def test_every_declared_symbol_is_exported_and_bound(fd):
@@ -132,6 +132,21 @@ def test_bad_pointers_are_rejected_before_any_launch(fd):
     assert lib.fdas_status_string(-3) == b"workspace too small"
     assert lib.fdas_device_status(None, 0) == -1
     assert lib.fdas_check_wait_timeout(None) == -1
+    tf, el = C.c_double(), C.c_float()
+    assert lib.fdas_measure_fp32_peak(50.0, None, C.byref(el)) == -1
+    assert lib.fdas_measure_fp32_peak(5.0, C.byref(tf), C.byref(el)) == -1
+    assert lib.fdas_measure_fp32_peak(5000.0, C.byref(tf), C.byref(el)) == -1
+
+
+def test_timeout_status_code(fd):
+    """FDAS_ERR_TIMEOUT (-5) is declared in the header, bound, and has its own message."""
+    from paper_1806_01556_gb300 import _lib
+
+    text = open(HEADER).read()
+    assert re.search(r"#define FDAS_ERR_TIMEOUT \(-5\)", text)
+    assert _lib.FDAS_ERR_TIMEOUT == -5
+    assert fd.lib().fdas_status_string(-5) == b"a kernel gave up on a bounded device wait"
+    assert fd.lib().fdas_status_string(-6) == b"unknown status"
 
 
 class _NullStream:
@@ -194,6 +209,18 @@ def test_batch_arguments_are_checked_on_the_host(fd):
     items[1].d_plane = fake
     hh = fd.Params(harm_index=1).c()  # the batched launches index by fundamental only
     assert lib.fdas_search_batch(C.byref(hh), C.cast(items, vp), 2, *args, ws, None, None) == -2
+    # The batched harmonic sum reads planes only: a NULL spectrum is fine, everything else is checked.
+    items[0].d_spec = items[1].d_spec = 0
+    hs = (vp(fake), vp(fake))  # d_thresh, d_ws
+    assert lib.fdas_harmonic_sum_batch(C.byref(hh), C.cast(items, vp), 2, *hs, ws, None) == -2
+    assert lib.fdas_harmonic_sum_batch(C.byref(p), C.cast(items, vp), 0, *hs, ws, None) == -1
+    assert lib.fdas_harmonic_sum_batch(C.byref(p), C.cast(items, vp), 2, *hs, ws - 1, None) == -3
+    assert lib.fdas_harmonic_sum_batch(C.byref(p), C.cast(items, vp), 2, vp(0), vp(fake), ws, None) == -1
+    items[1].d_plane = fake + 4
+    assert lib.fdas_harmonic_sum_batch(C.byref(p), C.cast(items, vp), 2, *hs, ws, None) == -1
+    items[1].d_plane = fake
+    items[1].d_counts = 0
+    assert lib.fdas_harmonic_sum_batch(C.byref(p), C.cast(items, vp), 2, *hs, ws, None) == -1
 
 
 def test_server_arguments_are_checked_on_the_host(fd):
@@ -267,3 +294,26 @@ def test_bench_path_roofline_is_the_slower_floor():
     assert r["bound"] == "hbm" and r["ms_at_roofline"] == r["ms_bytes"] and r["frac"] == r["ms_bytes"] / 1.0
     fast = bench.path_roofline(n, 421, 1.0, 1e9, "test")  # absurd bandwidth: the flops bound
     assert fast["bound"] == "alu" and fast["ms_at_roofline"] == fast["ms_flop"]
+
+
+def test_bench_oracle_pool_equals_the_oracle():
+    """The CPU baseline's split of the oracle plane over worker processes (column blocks computed from
+    bins widened by the half width) equals the oracle's plane_ols on the whole spectrum, and the
+    harmonic sum after it equals Algorithm 1 on that plane."""
+    import bench
+    import synth
+    from oracle import correlate, harmonic
+
+    n = 9000
+    rng = np.random.default_rng(3)
+    x = synth.complex_noise(rng, n) + synth.tone_spectrum(n, [synth.Tone(1500, 4, 15.0, 4)])
+    pool = bench.OraclePool(n, workers=3)
+    try:
+        _, _, res = pool.run(x)
+        got = np.ndarray((85, n), dtype=np.float32, buffer=pool._shm[1].buf).copy()
+        ref = correlate.plane_ols(x, pool.bank, 2048).astype(np.float32)
+        want = harmonic.detect(ref, pool.ta, 8, 0xFF, 200)
+    finally:
+        pool.close()
+    assert np.allclose(got, ref, rtol=2e-7, atol=0)
+    assert list(res.counts) == list(want.counts) and res.counts[0] > 0

@@ -1,11 +1,20 @@
-"""GPU: the batched form (fdas_search_batch, the graph-replayed plan, the autotuner) against
-fdas_search on each spectrum alone. Same kernels, same arithmetic: every output must be identical."""
+"""GPU: the batched form (fdas_search_batch, fdas_harmonic_sum_batch, the graph-replayed plan, the
+autotuner).
+
+Against the FP64 oracle (the paper's Sec. 3.5, many input arrays through one device):
+* every spectrum's plane of an uneven batch, elementwise, at the 1e-4 floored bar;
+* its candidates from the batched search within the plane tolerance of Algorithm 1 on the oracle plane;
+* the batched harmonic-sum kernels fed the oracle's float32 planes: candidates, counts and peaks bit
+  for bit.
+Against fdas_search on each spectrum alone: every output identical (same arithmetic).
+"""
 import numpy as np
 import pytest
 import torch
 
 import synth
-from oracle import thresholds
+from oracle import correlate, harmonic, thresholds
+from parity_helpers import REL_TOL, assert_candidates_within_tolerance, assert_same_candidates, plane_rel
 
 pytestmark = pytest.mark.gpu
 
@@ -133,3 +142,68 @@ def test_batch_of_the_maximum_count(fd):
     for b, r in zip(sample, ref):
         assert _same_written(r, _written(batch, b)), b
     plan.close()
+
+
+# Lengths on both sides of segment boundaries (L = 1628 kept outputs per segment), a single bin, and
+# one spectrum near 2^18 bins.
+ORACLE_LENGTHS = [1, 1628, 1629, 3256, 3257, 20011, 262139]
+
+
+@pytest.fixture(scope="module")
+def oracle_batch(bank):
+    rng = np.random.default_rng(13)
+    specs, planes = [], []
+    for n in ORACLE_LENGTHS:
+        x = synth.complex_noise(rng, n)
+        if n > 5000:
+            x = x + synth.tone_spectrum(n, [synth.Tone(n // 7, int(rng.integers(-5, 6)), 15.0, 8)])
+        x = x.astype(np.complex64)
+        specs.append(x)
+        planes.append(correlate.plane_ols(x, bank, 2048))
+    return specs, planes
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_batch_against_the_oracle(fd, oracle_batch, precision):
+    """fdas_search_batch on an uneven batch: each plane against the oracle, and each spectrum's
+    candidates (8 planes, 6 sigma) against Algorithm 1 on the oracle plane, within tolerance."""
+    specs, planes = oracle_batch
+    p = fd.Params(precision=precision, cand_cap=4096)
+    ta = thresholds.threshold_array(8, 85, sigma=6.0)
+    batch = fd.Batch(p, ORACLE_LENGTHS, thresh=ta)
+    for b, x in enumerate(specs):
+        batch.specs[b].copy_(torch.from_numpy(x))
+    batch.search()
+    torch.cuda.synchronize()
+    checked = 0
+    for b, n in enumerate(ORACLE_LENGTHS):
+        mx, rms = plane_rel(batch.planes[b][:, :n].cpu().numpy(), planes[b])
+        print(f"precision {precision} n={n}: plane rel max {mx:.2e} rms {rms:.2e}")
+        assert mx <= REL_TOL
+        cands, counts, _ = batch.results(b)
+        checked += assert_candidates_within_tolerance(cands, counts, planes[b], ta, 8, p.harm_mask, p.cand_cap)
+    assert checked > 50
+    assert fd.fdas_device_status() == 0
+
+
+@pytest.mark.parametrize(
+    "kw,sigma",
+    [(dict(), 6.0), (dict(harm_mask=0b10001011, cand_cap=300), 4.0), (dict(n_harm=16, harm_mask=0xFFFF, cand_cap=64), 3.5)],
+)
+def test_batched_harmonic_sum_on_oracle_planes_is_bit_exact(fd, oracle_batch, kw, sigma):
+    """fdas_harmonic_sum_batch (the batched kernels: job lookup by binary search, per-spectrum CTA
+    tables, the single-plane launch, per-(plane, spectrum) finalize) fed the oracle's float32 planes
+    returns Algorithm 1's candidates, counts and peaks bit for bit, for every spectrum."""
+    _, planes = oracle_batch
+    p = fd.Params(**kw)
+    ta = thresholds.threshold_array(p.n_harm, 85, sigma=sigma)
+    batch = fd.Batch(p, ORACLE_LENGTHS, thresh=ta)
+    for b, n in enumerate(ORACLE_LENGTHS):
+        batch.planes[b].fill_(1e30)  # the columns past n must never be read
+        batch.planes[b][:, :n] = torch.from_numpy(planes[b].astype(np.float32)).cuda()
+    batch.harmonic_sum()
+    torch.cuda.synchronize()
+    for b in range(len(ORACLE_LENGTHS)):
+        ref = harmonic.detect(planes[b].astype(np.float32), ta, p.n_harm, p.harm_mask, p.cand_cap)
+        cands, counts, peaks = batch.results(b)
+        assert_same_candidates(cands, counts, peaks, ref, p.harm_mask)

@@ -13,14 +13,9 @@ import torch
 import synth
 from oracle import correlate, harmonic, templates, thresholds
 
+from parity_helpers import REL_TOL, assert_candidates_within_tolerance, assert_same_candidates, plane_rel
+
 pytestmark = pytest.mark.gpu
-
-REL_TOL = 1e-4
-
-
-def plane_rel(gpu, ref):
-    rel = np.abs(gpu.astype(np.float64) - ref) / np.maximum(ref, ref.mean())
-    return rel.max(), np.sqrt(np.mean(rel**2))
 
 
 def run_convolve(fd, p, spec, ld=None, fill=np.nan):
@@ -50,18 +45,6 @@ def run_harmonic(fd, p, plane32, thresh, ld=None):
     torch.cuda.synchronize()
     counts = counts.cpu().numpy().astype(np.uint32)
     return fd.decode_cands(cands.cpu().numpy(), counts, p.cand_cap), counts, peaks.cpu().numpy().view(fd.CAND_DTYPE)
-
-
-def assert_same_candidates(got_cands, got_counts, got_peaks, ref, mask):
-    assert [int(c) for c in got_counts] == [int(c) for c in ref.counts]
-    for k, (g, r) in enumerate(zip(got_cands, ref.cands), start=1):
-        assert len(g) == len(r), k
-        assert np.array_equal(g["power"].view(np.uint32), r["power"].view(np.uint32)), k
-        assert np.array_equal(g["i"], r["i"]) and np.array_equal(g["j"], r["j"]), k
-        assert np.all(g["k"] == k)
-    for k, (g, r) in enumerate(zip(got_peaks, ref.peaks), start=1):
-        assert (np.float32(g["power"]).view(np.uint32), int(g["i"]), int(g["j"])) == (
-            np.float32(r[0]).view(np.uint32), r[1], r[2]), k
 
 
 # ---------------------------------------------------------------- templates
@@ -289,6 +272,22 @@ def test_search_candidates_match_oracle_within_tolerance(fd, small_case):
         for q in set(r) - set(g):
             assert r[q] <= ta[k - 1, 0] * (1 + tol)
     assert (int(cands[0][0]["i"]), int(cands[0][0]["j"])) == (20, 12000)
+
+
+def test_search_candidates_match_oracle_at_full_size(fd, ska_case):
+    """fdas_search at N = 2^21 in the bench's configuration (FP32, HP_1 of the single-plane rows taken
+    inside the convolution, row groups concurrent): every candidate of all 8 planes at the 6-sigma
+    thresholds against Algorithm 1 on the oracle plane, within the plane tolerance."""
+    wl, ref = ska_case
+    p = fd.Params(cand_cap=4096)
+    ta = thresholds.threshold_array(8, 85, sigma=6.0)
+    s = fd.Searcher(p, wl.n, thresh=ta)
+    s.search(torch.from_numpy(wl.spectrum).cuda(), wl.n)
+    torch.cuda.synchronize()
+    cands, counts, _ = s.results()
+    checked = assert_candidates_within_tolerance(cands, counts, ref, ta, 8, 0xFF, p.cand_cap)
+    print(f"N=2^21: {checked} candidates checked, counts {list(counts)}")
+    assert counts[0] > 100 and counts[7] > 10
 
 
 def test_no_bounded_wait_gave_up(fd, small_case):

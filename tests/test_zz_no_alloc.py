@@ -30,10 +30,14 @@ def _host(bufs):
     return tuple(b.cpu().numpy().tobytes() for b in bufs)
 
 
-def test_noalloc_matches_workspace_entry_point_on_two_calls(fd):
-    p = fd.Params()  # 8 harmonic planes, the most the static scratch holds
+@pytest.mark.parametrize("kw", [dict(), dict(harm_index=1), dict(harm_mask=0b10100100)],
+                         ids=["fundamental", "highest", "sparse-mask"])
+def test_noalloc_matches_workspace_entry_point_on_two_calls(fd, kw):
+    """Both indexings of the harmonic planes, and a mask that reports only planes 3, 6 and 8."""
+    p = fd.Params(**kw)  # 8 harmonic planes, the most the static scratch holds
     n = 1 << 15
     ta = torch.from_numpy(thresholds.threshold_array(8, 85, sigma=3.0)).cuda()
+    free = []
     for seed in (31, 32):  # two calls in a row, different planes
         plane = torch.from_numpy(synth.exponential_plane(np.random.default_rng(seed), 85, n)).cuda()
         ws_bytes = fd.fdas_workspace_bytes(p, n)
@@ -41,11 +45,20 @@ def test_noalloc_matches_workspace_entry_point_on_two_calls(fd):
         ref = _buffers(p, n)
         fd.fdas_harmonic_sum(p, plane, n, n, ta, *ref, ws, ws_bytes)
         got = _buffers(p, n)
+        torch.cuda.synchronize()
+        before = torch.cuda.mem_get_info()[0]
         fd.fdas_harmonic_sum_noalloc(p, plane, n, n, ta, *got)
         torch.cuda.synchronize()
+        free.append((before, torch.cuda.mem_get_info()[0]))
         r, g = _host(ref), _host(got)
-        assert np.frombuffer(r[1], np.int32)[0] > 200  # many crossings: the top-200 selection is exercised
+        counts = np.frombuffer(r[1], np.int32)
+        reported = [k for k in range(8) if (p.harm_mask >> k) & 1]
+        assert max(counts[k] for k in reported) > 200  # many crossings: the top-200 selection is exercised
+        assert all(counts[k] == 0 for k in range(8) if k not in reported)
         assert g == r
+    # The second call takes no device memory at all (the first one may load the library's scratch
+    # array, with CUDA's lazy module loading).
+    assert free[1][0] == free[1][1]
 
 
 def test_noalloc_rejects_more_planes_than_its_scratch_holds(fd):
