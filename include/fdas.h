@@ -116,6 +116,12 @@ fdas_status fdas_check_params(const fdas_params *p);
 /* Human-readable name of a status code. The string is static. */
 const char *fdas_status_string(fdas_status s);
 
+/* The last CUDA error that this thread's calls met (behind an FDAS_ERR_CUDA, or inside a call that
+ * recovered from it): the CUDA error's name and message, and the library function and source line
+ * that saw it. Empty if there was none. The string is thread-local and stays valid until this
+ * thread's next library call. No counterpart in the paper. */
+const char *fdas_last_error(void);
+
 /* Device-side status of the current device: bit FDAS_DEV_WAIT_TIMEOUT is set when a kernel gave up
  * on a bounded wait (the convolution waits on an mbarrier for each template's bulk copy, for about
  * one second at most). Such a kernel still ends, but its outputs are not valid. The paper has no

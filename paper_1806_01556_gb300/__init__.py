@@ -60,6 +60,10 @@ assert CAND_DTYPE.itemsize == C.sizeof(_lib.fdas_cand)
 class FdasError(RuntimeError):
     def __init__(self, status: int, what: str):
         msg = lib().fdas_status_string(status).decode()
+        if status == _lib.FDAS_ERR_CUDA:
+            detail = lib().fdas_last_error().decode()
+            if detail:
+                msg += f": {detail}"
         super().__init__(f"{what}: {msg} ({status})")
         self.status = status
 

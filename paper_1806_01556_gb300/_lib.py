@@ -87,6 +87,7 @@ SIGNATURES = {
     "fdas_default_params": (None, [P]),
     "fdas_check_params": (C.c_int, [P]),
     "fdas_status_string": (C.c_char_p, [C.c_int]),
+    "fdas_last_error": (C.c_char_p, []),
     "fdas_device_status": (C.c_int, [C.POINTER(C.c_uint32), C.c_int]),
     "fdas_set_device_status": (C.c_int, [C.c_uint32]),
     "fdas_measure_fp32_peak": (C.c_int, [C.c_float, C.POINTER(C.c_double), C.POINTER(C.c_float)]),

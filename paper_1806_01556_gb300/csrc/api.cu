@@ -3,6 +3,7 @@
 #include <cuda.h>  // driver API types only; the entry points are looked up through the runtime
 
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <mutex>
 
@@ -20,7 +21,13 @@ fdas_status check_shape(const fdas_params *p, size_t n, size_t ld) {
     return FDAS_OK;
 }
 
-fdas_status cuda_status(cudaError_t e) { return e == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA; }
+#define cuda_status(e) FDAS_STATUS(e)
+
+struct LastError {
+    cudaError_t code;
+    char text[320];
+};
+thread_local LastError g_last_error{cudaSuccess, {0}};
 
 // S_k(x) = P(Gamma(k,1) > x) = exp(-x) sum_{m<k} x^m / m!, integer k >= 1.
 double gamma_survival(int k, double x) {
@@ -47,6 +54,26 @@ double gamma_threshold(int k, double p) {
 }
 
 }  // namespace
+
+cudaError_t fdas::note(cudaError_t e, const char *where, int line) {
+    if (e == cudaSuccess) return e;
+    // An outer frame passing on the error a deeper call recorded keeps the deeper location.
+    if (e != g_last_error.code) {
+        g_last_error.code = e;
+        std::snprintf(g_last_error.text, sizeof(g_last_error.text), "%s (%s) in %s, line %d", cudaGetErrorName(e),
+                      cudaGetErrorString(e), where, line);
+    }
+    // The runtime keeps the error as this thread's last error too; clear it, so that a later launch
+    // check (cudaGetLastError) does not report it again. A sticky error stays regardless.
+    (void)cudaGetLastError();
+    return e;
+}
+
+fdas_status fdas::fail(cudaError_t e, const char *where, int line) {
+    if (e == cudaSuccess) return FDAS_OK;
+    note(e, where, line);
+    return FDAS_ERR_CUDA;
+}
 
 cudaError_t fdas::current_context_id(unsigned long long *id) {
     // cuCtxGetCurrent and cuCtxGetId from the driver, through the runtime (no link to libcuda).
@@ -131,6 +158,8 @@ fdas_status fdas_check_params(const fdas_params *p) {
     return FDAS_OK;
 }
 
+const char *fdas_last_error(void) { return g_last_error.text; }
+
 const char *fdas_status_string(fdas_status s) {
     switch (s) {
         case FDAS_OK: return "ok";
@@ -146,24 +175,24 @@ const char *fdas_status_string(fdas_status s) {
 fdas_status fdas_device_status(uint32_t *flags, int clear) {
     if (!flags) return FDAS_ERR_INVALID_ARG;
     unsigned v = 0u;
-    if (fdas::device_status(&v, clear != 0) != cudaSuccess) return FDAS_ERR_CUDA;
+    if (const fdas_status st = cuda_status(fdas::device_status(&v, clear != 0))) return st;
     *flags = v;
     return FDAS_OK;
 }
 
 fdas_status fdas_set_device_status(uint32_t flags) {
-    return fdas::set_device_status(flags) == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
+    return cuda_status(fdas::set_device_status(flags));
 }
 
 fdas_status fdas_measure_fp32_peak(float ms, double *tflops, float *elapsed_ms) {
     if (!tflops || !elapsed_ms || !(ms >= 10.0f) || ms > 2000.0f) return FDAS_ERR_INVALID_ARG;
-    return fdas::measure_fp32_peak(ms, tflops, elapsed_ms) == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
+    return cuda_status(fdas::measure_fp32_peak(ms, tflops, elapsed_ms));
 }
 
 fdas_status fdas_check_wait_timeout(uint32_t *flags) {
     if (!flags) return FDAS_ERR_INVALID_ARG;
     unsigned v = 0u;
-    if (fdas::check_wait_timeout(&v) != cudaSuccess) return FDAS_ERR_CUDA;
+    if (const fdas_status st = cuda_status(fdas::check_wait_timeout(&v))) return st;
     *flags = v;
     return FDAS_OK;
 }
@@ -202,7 +231,7 @@ fdas_status fdas_make_templates(const fdas_params *p, void *d_tmpl, fdas_stream_
     if (!d_tmpl || !aligned16(d_tmpl)) return FDAS_ERR_INVALID_ARG;
     // The harmonic sum's auxiliary streams for this thread and stream, made here so that a later
     // graph capture of a search on the same stream finds them.
-    if (fdas::prepare_streams(stream) != cudaSuccess) return FDAS_ERR_CUDA;
+    if (const fdas_status st = cuda_status(fdas::prepare_streams(stream))) return st;
     return cuda_status(fdas::launch_templates(*p, d_tmpl, stream));
 }
 
@@ -246,7 +275,7 @@ fdas_status fdas_search_convolve(const fdas_params *p, const void *d_spec, size_
     const Geometry g = fdas::geometry(*p);
     const fdas::HsWorkspace ws = fdas::hs_workspace(d_ws, p->n_harm);
     cudaError_t e = fdas::launch_hs_reset(*p, ws, stream);
-    if (e != cudaSuccess) return FDAS_ERR_CUDA;
+    if (e != cudaSuccess) return cuda_status(e);
     const float2 *spec = static_cast<const float2 *>(d_spec);
     const float2 *tmpl = static_cast<const float2 *>(d_tmpl);
     if (g.precision == FDAS_FP32 && p->harm_index == FDAS_INDEX_FUNDAMENTAL)
@@ -302,7 +331,7 @@ fdas_status fdas_search_host(const fdas_params *p, const void *h_spec, size_t n,
     unsigned flags[2] = {0u, 0u};
     cudaError_t e = fdas::device_status_async(flags, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-    if (e != cudaSuccess) return FDAS_ERR_CUDA;
+    if (e != cudaSuccess) return cuda_status(e);
     return ((flags[0] | flags[1]) & FDAS_DEV_WAIT_TIMEOUT) ? FDAS_ERR_TIMEOUT : FDAS_OK;
 }
 
@@ -317,18 +346,18 @@ fdas_status fdas_search_host_async(const fdas_params *p, const void *h_spec, siz
     if ((st = check_shape(p, n, ld)) != FDAS_OK) return st;
     if (!d_spec || !aligned16(d_spec)) return FDAS_ERR_INVALID_ARG;
     cudaError_t e = cudaMemcpyAsync(d_spec, h_spec, n * 8u, cudaMemcpyHostToDevice, stream);
-    if (e != cudaSuccess) return FDAS_ERR_CUDA;
+    if (e != cudaSuccess) return cuda_status(e);
     st = fdas_search(p, d_spec, n, d_tmpl, d_plane, ld, d_thresh, d_cands, d_counts, d_peaks, d_ws, ws_bytes, stream);
     if (st != FDAS_OK) return st;
     const size_t cand_bytes = (size_t)p->n_harm * p->cand_cap * sizeof(fdas_cand);
     if ((e = cudaMemcpyAsync(h_cands, d_cands, cand_bytes, cudaMemcpyDeviceToHost, stream)) != cudaSuccess)
-        return FDAS_ERR_CUDA;
+        return cuda_status(e);
     if ((e = cudaMemcpyAsync(h_counts, d_counts, p->n_harm * sizeof(uint32_t), cudaMemcpyDeviceToHost, stream)) !=
         cudaSuccess)
-        return FDAS_ERR_CUDA;
+        return cuda_status(e);
     if (h_peaks && (e = cudaMemcpyAsync(h_peaks, d_peaks, p->n_harm * sizeof(fdas_cand), cudaMemcpyDeviceToHost,
                                         stream)) != cudaSuccess)
-        return FDAS_ERR_CUDA;
+        return cuda_status(e);
     return FDAS_OK;
 }
 

@@ -166,7 +166,7 @@ fdas_status fdas_search_batch(const fdas_params *p, const fdas_batch_item *items
     if (e == cudaSuccess) e = prepare();
     if (e == cudaSuccess) e = launch_batch(*p, *t, d_tmpl, d_thresh, sms, c, stream);
     delete t;
-    return e == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
+    return FDAS_STATUS(e);
 }
 
 fdas_status fdas_harmonic_sum_batch(const fdas_params *p, const fdas_batch_item *items, int count,
@@ -180,7 +180,7 @@ fdas_status fdas_harmonic_sum_batch(const fdas_params *p, const fdas_batch_item 
     if (e == cudaSuccess)
         e = fdas::launch_harmonic_batch(*p, t->hs, t->total_16k, t->total_12k, t->total_4k, d_thresh, stream, false);
     delete t;
-    return e == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
+    return FDAS_STATUS(e);
 }
 
 fdas_status fdas_batch_plan_create(const fdas_params *p, const fdas_batch_item *items, int count, const void *d_tmpl,
@@ -223,22 +223,22 @@ fdas_status fdas_batch_plan_launch(fdas_batch_plan *plan, fdas_stream_t stream) 
         // this thread and this private stream, so searches that other threads run meanwhile neither
         // join the graph nor break the capture.
         cudaStream_t cap = plan->cap;
-        cudaError_t e = fdas::prepare_streams(cap);
-        if (e != cudaSuccess) return FDAS_ERR_CUDA;
-        e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        cudaError_t e = FDAS_NOTE(fdas::prepare_streams(cap));
+        if (e != cudaSuccess) return FDAS_STATUS(e);
+        e = FDAS_NOTE(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
         if (e == cudaSuccess) {
-            const cudaError_t le = launch_batch(plan->p, plan->tables, plan->d_tmpl, plan->d_thresh, plan->sms,
-                                                plan->cfg, cap);
-            e = cudaStreamEndCapture(cap, &plan->graph);
+            const cudaError_t le = FDAS_NOTE(launch_batch(plan->p, plan->tables, plan->d_tmpl, plan->d_thresh,
+                                                          plan->sms, plan->cfg, cap));
+            e = FDAS_NOTE(cudaStreamEndCapture(cap, &plan->graph));
             if (le != cudaSuccess) e = le;
         }
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&plan->exec, plan->graph, 0);
+        if (e == cudaSuccess) e = FDAS_NOTE(cudaGraphInstantiate(&plan->exec, plan->graph, 0));
         if (e != cudaSuccess) {
             drop_graph(plan);
-            return FDAS_ERR_CUDA;
+            return FDAS_STATUS(e);
         }
     }
-    return cudaGraphLaunch(plan->exec, stream) == cudaSuccess ? FDAS_OK : FDAS_ERR_CUDA;
+    return FDAS_STATUS(cudaGraphLaunch(plan->exec, stream));
 }
 
 fdas_status fdas_batch_plan_tune(fdas_batch_plan *plan, fdas_stream_t stream, fdas_launch_config *chosen,
@@ -248,7 +248,9 @@ fdas_status fdas_batch_plan_tune(fdas_batch_plan *plan, fdas_stream_t stream, fd
     static const int kCtas[] = {0, 2};
     static const int kTpi[] = {0, 43, 29, 17};
     cudaEvent_t a = nullptr, b = nullptr;
-    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return FDAS_ERR_CUDA;
+    cudaError_t ce = cudaEventCreate(&a);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&b);
+    if (ce != cudaSuccess) return FDAS_STATUS(ce);
     fdas_launch_config best{0, 0};
     float best_ms = -1.0f;
     Tables *t = new (std::nothrow) Tables;
@@ -274,12 +276,12 @@ fdas_status fdas_batch_plan_tune(fdas_batch_plan *plan, fdas_stream_t stream, fd
     delete t;
     cudaEventDestroy(a);
     cudaEventDestroy(b);
-    if (e != cudaSuccess) return FDAS_ERR_CUDA;
+    if (e != cudaSuccess) return FDAS_STATUS(e);
     // The timed launches have finished: a kernel that gave up on a bounded wait shows in the status.
     unsigned flags[2] = {0u, 0u};
     e = fdas::device_status_async(flags, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-    if (e != cudaSuccess) return FDAS_ERR_CUDA;
+    if (e != cudaSuccess) return FDAS_STATUS(e);
     if ((flags[0] | flags[1]) & FDAS_DEV_WAIT_TIMEOUT) return FDAS_ERR_TIMEOUT;
     plan->cfg = best;
     build_tables(plan->p, plan->items, plan->count, plan->d_ws, best.templates_per_item, &plan->tables);

@@ -9,6 +9,14 @@
 
 namespace fdas {
 
+// The last CUDA error met on this thread (fdas_last_error): note() records e with the function and
+// line that met it and returns e unchanged; fail() turns e into a status, recording it unless the
+// record already holds the same error from a deeper call.
+cudaError_t note(cudaError_t e, const char *where, int line);
+fdas_status fail(cudaError_t e, const char *where, int line);
+#define FDAS_NOTE(e) ::fdas::note((e), __func__, __LINE__)
+#define FDAS_STATUS(e) ::fdas::fail((e), __func__, __LINE__)
+
 // Derived sizes of one parameter set.
 struct Geometry {
     int n_temp;   // template rows

@@ -879,6 +879,9 @@ cudaError_t launch_hs_reset(const fdas_params &p, const HsWorkspace &ws, cudaStr
 //     behind one another on the auxiliary streams;
 //   - a set made for a context that was destroyed (cudaDeviceReset) is never used again: the key
 //     holds the driver's context id, which is unique for the life of the process.
+// The caller stream is keyed by its handle (no runtime query: most are not allowed on a stream that
+// is being captured). A handle that a destroyed stream had and a new stream got again finds that
+// stream's set, which is harmless: the set's own streams are valid, and only ordering is shared.
 // A thread keeps at most kAuxSets sets. When they are all taken, the least recently used set of the
 // current context is handed to the new caller stream, unless its streams are part of a capture in
 // progress; a set of another context is forgotten instead (its handles are not touched). Sets are
@@ -888,15 +891,21 @@ cudaError_t launch_hs_reset(const fdas_params &p, const HsWorkspace &ws, cudaStr
 constexpr int kAuxSets = 8;
 struct AuxSet {
     unsigned long long ctx;   // driver context id
-    unsigned long long sid;   // caller stream id (cudaStreamGetId)
+    cudaStream_t caller;      // caller stream handle
     unsigned long long used;  // last use, in this thread's call count
     cudaStream_t st[2];
     cudaEvent_t ev[3];
 };
 
+// True if s is being captured, or if the query fails (it does, for instance, on the legacy stream
+// while a blocking stream is captured); the failed query's error is cleared.
 bool stream_capturing(cudaStream_t s) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    return cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return true;
+    }
+    return cs != cudaStreamCaptureStatusNone;
 }
 
 cudaError_t make_aux(AuxSet &a) {
@@ -921,9 +930,8 @@ cudaError_t aux_set(cudaStream_t s, AuxSet **out) {
     thread_local AuxSet sets[kAuxSets];
     thread_local unsigned long long calls = 0;
     *out = nullptr;
-    unsigned long long ctx = 0, sid = 0;
-    cudaError_t e = current_context_id(&ctx);
-    if (e == cudaSuccess) e = cudaStreamGetId(s, &sid);
+    unsigned long long ctx = 0;
+    cudaError_t e = FDAS_NOTE(current_context_id(&ctx));
     if (e != cudaSuccess) return e;
     ++calls;
     AuxSet *hit = nullptr, *empty = nullptr, *other = nullptr, *lru = nullptr;
@@ -932,7 +940,7 @@ cudaError_t aux_set(cudaStream_t s, AuxSet **out) {
             if (!empty) empty = &a;
         } else if (a.ctx != ctx) {
             if (!other) other = &a;
-        } else if (a.sid == sid) {
+        } else if (a.caller == s) {
             hit = &a;
         } else if (!lru || a.used < lru->used) {
             lru = &a;
@@ -946,7 +954,7 @@ cudaError_t aux_set(cudaStream_t s, AuxSet **out) {
     if (stream_capturing(s)) return cudaSuccess;  // create nothing inside a capture
     AuxSet *slot = empty ? empty : other;
     if (slot) {
-        e = make_aux(*slot);
+        e = FDAS_NOTE(make_aux(*slot));
         if (e != cudaSuccess) return e;
     } else {
         // Reuse the least recently used set of this context whose streams no capture holds.
@@ -957,14 +965,14 @@ cudaError_t aux_set(cudaStream_t s, AuxSet **out) {
             }
             AuxSet *next = nullptr;
             for (AuxSet &a : sets)
-                if (a.st[0] && a.ctx == ctx && a.sid != sid && a.used > lru->used && (!next || a.used < next->used))
+                if (a.st[0] && a.ctx == ctx && a.caller != s && a.used > lru->used && (!next || a.used < next->used))
                     next = &a;
             lru = next;
         }
         if (!slot) return cudaSuccess;
     }
     slot->ctx = ctx;
-    slot->sid = sid;
+    slot->caller = s;
     slot->used = calls;
     *out = slot;
     return cudaSuccess;
@@ -981,24 +989,25 @@ cudaError_t side_by_side(cudaStream_t s, int count, bool concurrent, F &&launch)
     AuxSet *aux = nullptr;
     cudaError_t e = cudaSuccess;
     if (concurrent && count >= 2) e = aux_set(s, &aux);
+    if (e != cudaSuccess) return e;
     const bool fork = aux != nullptr;
     cudaStream_t st[3] = {s, s, s};
     if (fork) {
         st[1] = aux->st[0];
         st[2] = aux->st[1];
-        e = cudaEventRecord(aux->ev[0], s);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(st[1], aux->ev[0], 0);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(st[2], aux->ev[0], 0);
+        e = FDAS_NOTE(cudaEventRecord(aux->ev[0], s));
+        if (e == cudaSuccess) e = FDAS_NOTE(cudaStreamWaitEvent(st[1], aux->ev[0], 0));
+        if (e == cudaSuccess) e = FDAS_NOTE(cudaStreamWaitEvent(st[2], aux->ev[0], 0));
     }
     for (int k = 0; k < count && e == cudaSuccess; ++k) {
         launch(k, fork ? st[k == 0 ? 0 : (k & 1) ? 1 : 2] : s);
-        e = cudaGetLastError();
+        e = FDAS_NOTE(cudaGetLastError());
     }
     if (fork) {
-        if (e == cudaSuccess) e = cudaEventRecord(aux->ev[1], st[1]);
-        if (e == cudaSuccess) e = cudaEventRecord(aux->ev[2], st[2]);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, aux->ev[1], 0);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, aux->ev[2], 0);
+        if (e == cudaSuccess) e = FDAS_NOTE(cudaEventRecord(aux->ev[1], st[1]));
+        if (e == cudaSuccess) e = FDAS_NOTE(cudaEventRecord(aux->ev[2], st[2]));
+        if (e == cudaSuccess) e = FDAS_NOTE(cudaStreamWaitEvent(s, aux->ev[1], 0));
+        if (e == cudaSuccess) e = FDAS_NOTE(cudaStreamWaitEvent(s, aux->ev[2], 0));
     }
     return e;
 }

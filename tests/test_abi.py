@@ -147,6 +147,7 @@ def test_timeout_status_code(fd):
     assert _lib.FDAS_ERR_TIMEOUT == -5
     assert fd.lib().fdas_status_string(-5) == b"a kernel gave up on a bounded device wait"
     assert fd.lib().fdas_status_string(-6) == b"unknown status"
+    assert fd.lib().fdas_last_error() == b""  # no CUDA call has failed on this thread
 
 
 class _NullStream:
