@@ -363,6 +363,9 @@ def _search_both_ways(fd, p, spec, thresh, ld=None):
         (40000, dict(n_harm=16, harm_mask=0xFFFF), 3.5),
         (30000, dict(n_temp=9, z_min=-8, z_step=2, n_tap=129, n_harm=4, harm_mask=0xF), 3.0),
         (30000, dict(harm_index=1), 3.5),
+        (1628 * 7 + 5, dict(n_harm=16, harm_mask=0xFFFF, cand_cap=500), 3.0),
+        (65536, dict(n_harm=5, harm_mask=0b10110), 3.5),
+        (99991, dict(n_temp=255, z_min=-127, n_harm=12, harm_mask=0xFFF), 4.0),
     ],
 )
 def test_search_with_fused_hp1_equals_separate_calls(fd, n, kw, sigma):
