@@ -237,13 +237,15 @@ fdas_status fdas_convolve(const fdas_params *p, const void *d_spec, size_t n, co
  * Calls that share d_ws must not overlap on the device.
  * The kernels of one call may run side by side on two auxiliary streams of the library, forked from
  * and joined back into `stream` with events, so work enqueued on `stream` afterwards, and a graph
- * captured from `stream`, see the whole harmonic sum. There is one pair per host thread, CUDA
- * context and caller stream (up to 8 pairs per thread, the least recently used pair going to a new
- * caller stream), made at the first call that needs it or in fdas_make_templates on that stream, and
- * kept until the process exits. So calls from other threads, or on other streams, never share these
- * streams, and a capture in one thread records none of another thread's work. No pair is made while
- * `stream` is being captured: a captured call on a stream that has none runs its kernels on `stream`
- * alone, with the same results. A pair made before cudaDeviceReset is never used afterwards.
+ * captured from `stream`, see the whole harmonic sum. The pair belongs to the calling host thread and
+ * CUDA context and serves all of that thread's caller streams, so successive harmonic sums of one
+ * thread queue behind one another on it; it is made at the first call that needs it (or in
+ * fdas_make_templates) and kept until the process exits. Calls from other threads never share it, so a
+ * capture in one thread records none of another thread's work. While a pair takes part in a capture,
+ * it serves only calls on that capture's streams; another call of the same thread gets a second pair
+ * (up to 8 per thread). No pair is made while `stream` is being captured: a captured call that finds
+ * none runs its kernels on `stream` alone, with the same results. A pair made before cudaDeviceReset
+ * is never used afterwards.
  */
 fdas_status fdas_harmonic_sum(const fdas_params *p, const float *d_plane, size_t n, size_t ld,
                               const float *d_thresh, fdas_cand *d_cands, uint32_t *d_counts,

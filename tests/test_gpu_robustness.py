@@ -5,8 +5,9 @@
   the host: the test sets the device status word with fdas_set_device_status, so no kernel waits
   for anything that does not come.
 * A batch plan captured into a CUDA graph in one host thread while another thread runs eager
-  searches: both get their own results (each thread and caller stream has its own auxiliary
-  streams, and the capture is thread-local).
+  searches: both get their own results (each thread has its own auxiliary streams, and the capture
+  is thread-local). And within one thread: an eager search on one stream while a capture on another
+  stream is open does not use the auxiliary streams that joined the capture.
 * The FP32 peak diagnostic returns a plausible rate.
 """
 import threading
@@ -164,3 +165,34 @@ def test_fp32_peak_diagnostic(fd):
     tflops, ms = fd.fdas_measure_fp32_peak(50.0)
     assert 10.0 < ms < 1000.0
     assert 25.0 < tflops < 90.0, tflops
+
+
+def test_eager_search_beside_a_capture_in_the_same_thread(fd, small_case):
+    """One thread captures fdas_search on stream X and, while that capture is open, runs an eager
+    fdas_search on stream Y. The thread's auxiliary streams join X's capture, so the eager call must
+    take another pair: the eager results are right at once, and the graph replays to the same results."""
+    wl, _ = small_case
+    p = fd.Params()
+    ta = thresholds.threshold_array(p.n_harm, p.n_temp, sigma=3.0)
+    d_spec = torch.from_numpy(wl.spectrum).cuda()
+    ref = fd.Searcher(p, wl.n, thresh=ta)
+    ref.search(d_spec, wl.n)
+    torch.cuda.synchronize()
+    want = ref.results()
+    cap_s, eager_s = fd.Searcher(p, wl.n, thresh=ta), fd.Searcher(p, wl.n, thresh=ta)
+    x, y = torch.cuda.Stream(), torch.cuda.Stream()
+    cap_s.search(d_spec, wl.n, stream=x)  # eager warm-up on x
+    torch.cuda.synchronize()
+    for t in (cap_s.cands, cap_s.counts, cap_s.peaks):
+        t.zero_()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=x, capture_error_mode="thread_local"):
+        cap_s.search(d_spec, wl.n)  # captured on x
+        eager_s.search(d_spec, wl.n, stream=y)  # eager on y, while x's capture is open
+    y.synchronize()
+    _same_results(eager_s.results(), want)
+    g.replay()
+    torch.cuda.synchronize()
+    _same_results(cap_s.results(), want)
+    assert fd.fdas_device_status() == 0
