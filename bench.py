@@ -46,10 +46,10 @@ KERNEL_SOURCES = {
 # "harmonic.cu": the harmonic stage of an FP32 search (no single-plane launch); "harmonic.cu+k1":
 # the full harmonic sum, as the tensor-core forms run it.
 NCU_TRAFFIC = {
-    "convolve.cu": ("7e3875ec313c", 669.3e6),
-    "convolve_tc.cu": ("8df7e36a91d1", 669.2e6),
-    "harmonic.cu": ("261a66b0b929", 1434.3e6),
-    "harmonic.cu+k1": ("261a66b0b929", 1786.8e6),
+    "convolve.cu": ("784ed10db7cb", 671.7e6),
+    "convolve_tc.cu": ("442262980ef0", 670.1e6),
+    "harmonic.cu": ("a41a8632bd8a", 1436.6e6),
+    "harmonic.cu+k1": ("a41a8632bd8a", 1789.1e6),
 }
 
 
