@@ -236,6 +236,23 @@ __device__ __forceinline__ int group_row_offset(int y, int lo) {
     return (y & 1) ? a : -a;
 }
 
+// Row i of the group |i| <= hi (the rows with the most planes) in family order: first i = 0, then
+// the positive rows and then the negative ones, each sign by families b, 2b, 4b, ... for odd b
+// (1, 2, 4, 8, 3, 6, 5, 7 for hi = 8). Term l of row i reads plane row c + l i, so rows of one family
+// read many of the same plane rows (rows 1, 2, 4 read 16 distinct rows, not 24); launched next to
+// one another, they find more of those rows in L2.
+__device__ __forceinline__ int family_row_offset(int y, int hi) {
+    if (y == 0) return 0;
+    const int sgn = y <= hi ? 1 : -1;
+    int k = (y - 1) % hi;
+    for (int b = 1; b <= hi; b += 2)
+        for (int m = b; m <= hi; m *= 2) {
+            if (k == 0) return sgn * m;
+            --k;
+        }
+    return sgn * hi;
+}
+
 // One launch per group of rows sharing klast = min(n_harm, floor(c/|i|)) planes, so each kernel is
 // compiled for exactly its number of terms. Grid: (column blocks of 1024 fundamentals, rows of the group).
 __global__ void __launch_bounds__(kHsThreads, 4)
@@ -258,7 +275,7 @@ __global__ void __launch_bounds__(kHsThreads, KL <= 3 ? 4 : 2)
                unsigned mask, int n_harm, int lo, unsigned long long *__restrict__ raw, unsigned long long *counters,
                unsigned long long *peaks) {
     const int c = (n_temp - 1) / 2;
-    const int i = group_row_offset(blockIdx.y, lo);
+    const int i = lo == 0 ? family_row_offset(blockIdx.y, (int)(gridDim.y - 1) / 2) : group_row_offset(blockIdx.y, lo);
     const int ai = i < 0 ? -i : i;
     const int klast = ai == 0 ? n_harm : min(n_harm, c / ai);
     hs_row<KL, kChunksOne>(plane, n, ld, thresh, n_temp, mask, c, i, klast,
