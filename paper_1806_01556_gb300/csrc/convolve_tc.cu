@@ -330,8 +330,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
                 for (int hh = 0; hh < 2; ++hh) {
                     uint32_t xe[16], xo[16];  // own component (re if even lane, im if odd) of templates 0, 1
-                    tc::tmem_ld16(d1 + 16 * hh, xe);
-                    tc::tmem_ld16(d1 + 32 + 16 * hh, xo);
+                    tc::tmem_ld16x2(d1 + 16 * hh, xe, d1 + 32 + 16 * hh, xo);
 #pragma unroll
                     for (int i = 0; i < 16; i += 2) {
                         const int m1 = 16 * hh + i;
