@@ -121,9 +121,10 @@ __device__ __forceinline__ float2 w32(float2 v, int k) {
 
 // In-place inverse 32-point DFT, natural order: u[n] = sum_m v[m] e^{2 pi i m n / 32}. Radix 4 x 8:
 // m = a + 8 b, n = 4 c + d: 4-point DFTs over b, twiddles e^{2 pi i a d / 32}, 8-point DFTs over a.
+// Scalar sums here: the packed FP32x2 form measured slightly slower in this kernel.
 __device__ __forceinline__ void idft32(float2 (&v)[32]) {
 #pragma unroll
-    for (int a = 0; a < 8; ++a) dft4<true>(v[a], v[a + 8], v[a + 16], v[a + 24]);
+    for (int a = 0; a < 8; ++a) dft4<true, false>(v[a], v[a + 8], v[a + 16], v[a + 24]);
 #pragma unroll
     for (int a = 1; a < 8; ++a)
 #pragma unroll
@@ -134,7 +135,7 @@ __device__ __forceinline__ void idft32(float2 (&v)[32]) {
         float2 x[8];
 #pragma unroll
         for (int a = 0; a < 8; ++a) x[a] = v[a + 8 * d];
-        dft8<true>(x);
+        dft8<true, false>(x);
 #pragma unroll
         for (int c = 0; c < 8; ++c) u[4 * c + d] = x[c];
     }

@@ -1,7 +1,8 @@
 // Pieces shared by the overlap-save convolution kernels (FP32 and tensor-core forms): the
 // 2048-point FFT in registers (radix 16 x 16 x 8 Stockham passes through a padded shared-memory
-// buffer), the TMA bulk copy with its bounded mbarrier wait, and the work-item decomposition
-// (segment s of a spectrum with a range of templates). Everything here has internal linkage, so
+// buffer; the butterflies' complex sums as packed FP32x2 instructions, two lanes per issue slot),
+// the TMA bulk copy with its bounded mbarrier wait, and the work-item decomposition (segment s of a
+// spectrum with a range of templates). Everything here has internal linkage, so
 // each translation unit that includes it has its own copy, including its own status word.
 #pragma once
 #include "fdas_internal.cuh"
@@ -27,6 +28,17 @@ __device__ __forceinline__ float2 twiddle(float2 v, float2 w) {  // w = exp(-2 p
 }
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// The same sums as single packed FP32x2 instructions (two lanes per issue slot).
+__device__ __forceinline__ float2 cadd2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub2(float2 a, float2 b) {
+    unsigned long long x, y, d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(x) : "f"(a.x), "f"(a.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(y) : "f"(b.x), "f"(b.y));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(x), "l"(y));
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(d));
+    return r;
+}
 
 // Status bits set on the device (read with fdas_device_status): a bounded wait gave up.
 __device__ unsigned int g_device_status;
@@ -67,11 +79,13 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
 }
 
 // In-place 4-point DFT of (a, b, c, d) with sign exp(-+2 pi i / 4); outputs in natural order.
-template <bool INV>
+// PACKED: the complex sums as packed FP32x2 instructions (the +-i s3 terms stay scalar).
+template <bool INV, bool PACKED = true>
 __device__ __forceinline__ void dft4(float2 &a, float2 &b, float2 &c, float2 &d) {
-    const float2 s0 = cadd(a, c), s1 = csub(a, c), s2 = cadd(b, d), s3 = csub(b, d);
-    a = cadd(s0, s2);
-    c = csub(s0, s2);
+    const float2 s0 = PACKED ? cadd2(a, c) : cadd(a, c), s1 = PACKED ? csub2(a, c) : csub(a, c),
+                 s2 = PACKED ? cadd2(b, d) : cadd(b, d), s3 = PACKED ? csub2(b, d) : csub(b, d);
+    a = PACKED ? cadd2(s0, s2) : cadd(s0, s2);
+    c = PACKED ? csub2(s0, s2) : csub(s0, s2);
     if (!INV) {
         b = make_float2(s1.x + s3.y, s1.y - s3.x);  // s1 - i s3
         d = make_float2(s1.x - s3.y, s1.y + s3.x);  // s1 + i s3
@@ -125,18 +139,18 @@ __device__ __forceinline__ void dft16(float2 (&v)[16]) {
 }
 
 // 8-point DFT in registers, natural order in and out: radix 4 x 2.
-template <bool INV>
+template <bool INV, bool PACKED = true>
 __device__ __forceinline__ void dft8(float2 (&v)[8]) {
-    dft4<INV>(v[0], v[2], v[4], v[6]);
-    dft4<INV>(v[1], v[3], v[5], v[7]);
+    dft4<INV, PACKED>(v[0], v[2], v[4], v[6]);
+    dft4<INV, PACKED>(v[1], v[3], v[5], v[7]);
     v[3] = w16<INV, 2>(v[3]);  // W8^1
     v[5] = w16<INV, 4>(v[5]);  // W8^2
     v[7] = w16<INV, 6>(v[7]);  // W8^3
     float2 t[8];
 #pragma unroll
     for (int k1 = 0; k1 < 4; ++k1) {
-        t[k1] = cadd(v[2 * k1], v[2 * k1 + 1]);
-        t[k1 + 4] = csub(v[2 * k1], v[2 * k1 + 1]);
+        t[k1] = PACKED ? cadd2(v[2 * k1], v[2 * k1 + 1]) : cadd(v[2 * k1], v[2 * k1 + 1]);
+        t[k1 + 4] = PACKED ? csub2(v[2 * k1], v[2 * k1 + 1]) : csub(v[2 * k1], v[2 * k1 + 1]);
     }
 #pragma unroll
     for (int i = 0; i < 8; ++i) v[i] = t[i];
@@ -149,17 +163,18 @@ __device__ __forceinline__ void fft_passes_12(float2 (&v)[16], float2 *buf0, flo
                                               int tid, AfterFirstBarrier after_first_barrier, Sync sync) {
     dft16<INV>(v);
 #pragma unroll
-    for (int r = 0; r < 16; ++r) buf0[pad(16 * tid + r)] = v[r];
+    for (int r = 0; r < 16; ++r) (buf0 + 17 * tid)[r] = v[r];  // pad(16 tid + r)
     sync();
     after_first_barrier();
+    const float2 *src = buf0 + tid + (tid >> 4);  // pad(tid + 128 r) = tid + tid / 16 + 136 r
 #pragma unroll
-    for (int r = 0; r < 16; ++r) v[r] = buf0[pad(tid + 128 * r)];
+    for (int r = 0; r < 16; ++r) v[r] = src[136 * r];
 #pragma unroll
     for (int r = 1; r < 16; ++r) v[r] = twiddle<INV>(v[r], tw2[r]);
     dft16<INV>(v);
-    const int base = (tid >> 4) * 256 + (tid & 15);
+    float2 *dst = buf1 + (tid >> 4) * 272 + (tid & 15);  // pad(256 (tid / 16) + tid % 16 + 16 r)
 #pragma unroll
-    for (int r = 0; r < 16; ++r) buf1[pad(base + 16 * r)] = v[r];
+    for (int r = 0; r < 16; ++r) dst[17 * r] = v[r];
     sync();
 }
 template <bool INV, class AfterFirstBarrier>
@@ -172,7 +187,7 @@ __device__ __forceinline__ void fft_passes_12(float2 (&v)[16], float2 *buf0, flo
 template <bool INV>
 __device__ __forceinline__ void fft_pass_3(float2 (&u)[8], const float2 *buf1, const float2 (&tw3)[8], int b) {
 #pragma unroll
-    for (int r = 0; r < 8; ++r) u[r] = buf1[pad(b + 256 * r)];
+    for (int r = 0; r < 8; ++r) u[r] = (buf1 + b + (b >> 4))[272 * r];  // pad(b + 256 r)
 #pragma unroll
     for (int r = 1; r < 8; ++r) u[r] = twiddle<INV>(u[r], tw3[r]);
     dft8<INV>(u);
