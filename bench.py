@@ -607,22 +607,24 @@ def run_fdas(args):
         del pair
 
     # End to end from host memory, every step: the pinned spectrum in, the candidates, counts and
-    # peaks out. Headline: fdas_search_host_async on two searchers and streams in turn, so one
-    # spectrum's copies overlap the other's search; beside it, fdas_search_host one call at a time.
+    # peaks out. Headline: fdas_search_host_async on three searchers and streams in turn. A stream's
+    # copy in waits for that stream's previous search, which is then two spectra back and finished,
+    # so every copy overlaps the searches of the other two streams (with two streams about half of
+    # each 82 us copy stayed exposed). Beside it, fdas_search_host one call at a time.
     h_spec = torch.from_numpy(wl.spectrum).pin_memory()
-    duo = [s, fdas.Searcher(s.p, args.n, device=f"cuda:{local}")]
-    duo_streams = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)]
-    for k in range(4):
-        duo[k & 1].search_host_async(h_spec, args.n, duo_streams[k & 1])
+    trio = [s] + [fdas.Searcher(s.p, args.n, device=f"cuda:{local}") for _ in range(2)]
+    trio_streams = [torch.cuda.Stream(dev) for _ in range(3)]
+    for k in range(6):
+        trio[k % 3].search_host_async(h_spec, args.n, trio_streams[k % 3])
     torch.cuda.synchronize(dev)
     barrier()
     t0 = time.perf_counter()
     for k in range(args.steps):
-        duo[k & 1].search_host_async(h_spec, args.n, duo_streams[k & 1])
-    for st in duo_streams:
+        trio[k % 3].search_host_async(h_spec, args.n, trio_streams[k % 3])
+    for st in trio_streams:
         st.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
-    del duo[1]
+    del trio[1:]
     for _ in range(2):
         s.search_host(h_spec, args.n)
     barrier()
@@ -680,7 +682,7 @@ def run_fdas(args):
             "clocks": forms[head]["clocks"],
             "e2e": {"value": job_throughput(world, args.steps, e2e_s), "unit": "spectra/s",
                     "h2d_bytes_per_step": args.n * 8, "d2h_bytes_per_step": d2h,
-                    "api": "fdas_search_host_async, two searchers and streams in turn",
+                    "api": "fdas_search_host_async, three searchers and streams in turn",
                     "one_call_at_a_time": job_throughput(world, args.steps, e2e_sync_s)},
             "gpu_launches": search_launches(head, p.n_harm, p.n_temp, args.harm_index) * args.steps,
             "roofline": roof,

@@ -472,9 +472,11 @@ def test_search_captured_in_a_cuda_graph_equals_eager(fd, small_case, precision)
     assert fd.fdas_device_status() == 0
 
 
-def test_search_host_async_on_two_streams_equals_the_synchronous_call(fd, small_case):
-    """fdas_search_host_async on two searchers and streams in turn (copies of one spectrum overlapping
-    the other's search) leaves the same host results as fdas_search_host."""
+@pytest.mark.parametrize("m", [2, 3])
+def test_search_host_async_on_several_streams_equals_the_synchronous_call(fd, small_case, m):
+    """fdas_search_host_async on m searchers and streams in turn (copies of one spectrum overlapping
+    the others' searches; three is the pattern bench.py times) leaves the same host results as
+    fdas_search_host."""
     wl, _ = small_case
     p = fd.Params()
     ta = thresholds.threshold_array(p.n_harm, p.n_temp, sigma=3.0)
@@ -483,10 +485,10 @@ def test_search_host_async_on_two_streams_equals_the_synchronous_call(fd, small_
     ref.search_host(h, wl.n)
     want_c, want_n, want_p = ref.results(host=True)
     assert want_n.sum() > 0
-    pair = [fd.Searcher(p, wl.n, thresh=ta) for _ in range(2)]
-    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
-    for k in range(5):
-        pair[k % 2].search_host_async(h, wl.n, streams[k % 2])
+    pair = [fd.Searcher(p, wl.n, thresh=ta) for _ in range(m)]
+    streams = [torch.cuda.Stream() for _ in range(m)]
+    for k in range(2 * m + 1):
+        pair[k % m].search_host_async(h, wl.n, streams[k % m])
     torch.cuda.synchronize()
     for s in pair:
         got_c, got_n, got_p = s.results(host=True)
