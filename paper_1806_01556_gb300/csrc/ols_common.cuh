@@ -111,33 +111,6 @@ __device__ __forceinline__ float2 w16(float2 v) {
     return make_float2(fmaf(v.x, wr, -v.y * wi), fmaf(v.x, wi, v.y * wr));
 }
 
-// 16-point DFT in registers, natural order in and out: radix 4 x 4 with internal twiddles.
-template <bool INV>
-__device__ __forceinline__ void dft16(float2 (&v)[16]) {
-#pragma unroll
-    for (int n2 = 0; n2 < 4; ++n2) dft4<INV>(v[n2], v[4 + n2], v[8 + n2], v[12 + n2]);
-    // v[4 k1 + n2] *= W16^(n2 k1)
-    v[5] = w16<INV, 1>(v[5]);
-    v[6] = w16<INV, 2>(v[6]);
-    v[7] = w16<INV, 3>(v[7]);
-    v[9] = w16<INV, 2>(v[9]);
-    v[10] = w16<INV, 4>(v[10]);
-    v[11] = w16<INV, 6>(v[11]);
-    v[13] = w16<INV, 3>(v[13]);
-    v[14] = w16<INV, 6>(v[14]);
-    v[15] = w16<INV, 9>(v[15]);
-#pragma unroll
-    for (int k1 = 0; k1 < 4; ++k1) dft4<INV>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
-    // v[4 k1 + k2] holds X[k1 + 4 k2]: transpose the 4 x 4 register block.
-    float2 t[16];
-#pragma unroll
-    for (int k1 = 0; k1 < 4; ++k1)
-#pragma unroll
-        for (int k2 = 0; k2 < 4; ++k2) t[k1 + 4 * k2] = v[4 * k1 + k2];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = t[i];
-}
-
 // 8-point DFT in registers, natural order in and out: radix 4 x 2.
 template <bool INV, bool PACKED = true>
 __device__ __forceinline__ void dft8(float2 (&v)[8]) {
@@ -156,12 +129,100 @@ __device__ __forceinline__ void dft8(float2 (&v)[8]) {
     for (int i = 0; i < 8; ++i) v[i] = t[i];
 }
 
+// ---- Constant twiddles folded into the butterflies (FMA form) ----
+//
+// A twiddle w with Re w != 0 is w = s (1 + i t), s = Re w, t = Im w / s. The factor (1 + i t) costs
+// two FMAs, (x.r - t x.i, x.i + t x.r), and the real s rides on the FMA that adds the product into a
+// butterfly sum: a radix-4 butterfly whose first input carries no twiddle takes 22 FP32 instructions
+// instead of 28 (three complex products and 16 additions). The inverse transform uses
+// conj(w) = s (1 - i t). Used for the constant twiddles W16^m of the 16-point DFTs, whose s and t are
+// compile-time constants.
+
+// x (1 + i t) (forward) or x (1 - i t) (inverse).
+template <bool INV>
+__device__ __forceinline__ float2 mul_1it(float2 x, float t) {
+    const float u = INV ? -t : t;
+    return make_float2(fmaf(-u, x.y, x.x), fmaf(u, x.x, x.y));
+}
+// x W4: -i x (forward) or +i x (inverse).
+template <bool INV>
+__device__ __forceinline__ float2 mul_w4(float2 x) {
+    return INV ? make_float2(-x.y, x.x) : make_float2(x.y, -x.x);
+}
+
+// 4-point DFT of (a, sb b, sc c, sb mu d) in place, natural order: 16 FMAs.
+template <bool INV>
+__device__ __forceinline__ void r4_scaled(float2 &a, float2 &b, float2 &c, float2 &d, float sc, float mu, float sb) {
+    const float2 s0 = make_float2(fmaf(sc, c.x, a.x), fmaf(sc, c.y, a.y));
+    const float2 s1 = make_float2(fmaf(-sc, c.x, a.x), fmaf(-sc, c.y, a.y));
+    const float2 q = make_float2(fmaf(mu, d.x, b.x), fmaf(mu, d.y, b.y));
+    const float2 p = mul_w4<INV>(make_float2(fmaf(-mu, d.x, b.x), fmaf(-mu, d.y, b.y)));
+    a = make_float2(fmaf(sb, q.x, s0.x), fmaf(sb, q.y, s0.y));
+    c = make_float2(fmaf(-sb, q.x, s0.x), fmaf(-sb, q.y, s0.y));
+    b = make_float2(fmaf(sb, p.x, s1.x), fmaf(sb, p.y, s1.y));
+    d = make_float2(fmaf(-sb, p.x, s1.x), fmaf(-sb, p.y, s1.y));
+}
+
+// cos(2 pi m / 16) and tan(2 pi m / 16) for the constant m (cos != 0).
+template <int M>
+__device__ __forceinline__ constexpr float cos16() {
+    constexpr int m = M & 15;
+    static_assert(m != 4 && m != 12, "W16^4 and W16^12 are rotations");
+    constexpr float c1 = 0.92387953251128674f, s1 = 0.38268343236508977f, r = 0.70710678118654752f;
+    return m == 0 ? 1.f : m == 1 ? c1 : m == 2 ? r : m == 3 ? s1 : m == 5 ? -s1 : m == 6 ? -r : m == 7 ? -c1
+         : m == 8 ? -1.f : m == 9 ? -c1 : m == 10 ? -r : m == 11 ? -s1 : m == 13 ? s1 : m == 14 ? r : c1;
+}
+template <int M>
+__device__ __forceinline__ constexpr float tan16() {
+    constexpr int m = M & 15;
+    static_assert(m != 4 && m != 12, "W16^4 and W16^12 are rotations");
+    constexpr float t1 = 0.41421356237309505f, t3 = 2.4142135623730950f;
+    return (m & 7) == 0 ? 0.f : (m & 7) == 1 ? t1 : (m & 7) == 2 ? 1.f : (m & 7) == 3 ? t3 : (m & 7) == 5 ? -t3
+         : (m & 7) == 6 ? -1.f : -t1;
+}
+
+// 16-point DFT in registers, natural order in and out: the first radix-4 layer and the untwiddled
+// row of the second with packed sums, the three rows with constant twiddles W16^m in FMA form. Same
+// issue slots as dft16 with packed sums, 6 fewer FP32 pipe operations per twiddled row.
+template <bool INV>
+__device__ __forceinline__ void dft16_hyb(float2 (&v)[16]) {
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) dft4<INV>(v[n2], v[4 + n2], v[8 + n2], v[12 + n2]);
+    dft4<INV>(v[0], v[1], v[2], v[3]);
+    constexpr float c1 = cos16<1>(), c2 = cos16<2>(), c3 = cos16<3>(), c6 = cos16<6>(), c9 = cos16<9>();
+    {
+        v[5] = mul_1it<INV>(v[5], -tan16<1>());
+        v[6] = mul_1it<INV>(v[6], -tan16<2>());
+        v[7] = mul_1it<INV>(v[7], -tan16<3>());
+        r4_scaled<INV>(v[4], v[5], v[6], v[7], c2, c3 / c1, c1);
+    }
+    {
+        v[9] = mul_1it<INV>(v[9], -tan16<2>());
+        v[10] = mul_w4<INV>(v[10]);
+        v[11] = mul_1it<INV>(v[11], -tan16<6>());
+        r4_scaled<INV>(v[8], v[9], v[10], v[11], 1.f, c6 / c2, c2);
+    }
+    {
+        v[13] = mul_1it<INV>(v[13], -tan16<3>());
+        v[14] = mul_1it<INV>(v[14], -tan16<6>());
+        v[15] = mul_1it<INV>(v[15], -tan16<9>());
+        r4_scaled<INV>(v[12], v[13], v[14], v[15], c6, c9 / c3, c3);
+    }
+    float2 t[16];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) t[k1 + 4 * k2] = v[4 * k1 + k2];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = t[i];
+}
+
 // Passes 1 and 2 of the Stockham FFT: registers (A[tid + 128 r]) -> pass 1 -> buf0 -> pass 2 -> buf1.
 // `sync` synchronises the 128 threads that run the FFT (the whole CTA by default).
 template <bool INV, class AfterFirstBarrier, class Sync>
 __device__ __forceinline__ void fft_passes_12(float2 (&v)[16], float2 *buf0, float2 *buf1, const float2 (&tw2)[16],
                                               int tid, AfterFirstBarrier after_first_barrier, Sync sync) {
-    dft16<INV>(v);
+    dft16_hyb<INV>(v);
 #pragma unroll
     for (int r = 0; r < 16; ++r) (buf0 + 17 * tid)[r] = v[r];  // pad(16 tid + r)
     sync();
@@ -171,7 +232,7 @@ __device__ __forceinline__ void fft_passes_12(float2 (&v)[16], float2 *buf0, flo
     for (int r = 0; r < 16; ++r) v[r] = src[136 * r];
 #pragma unroll
     for (int r = 1; r < 16; ++r) v[r] = twiddle<INV>(v[r], tw2[r]);
-    dft16<INV>(v);
+    dft16_hyb<INV>(v);
     float2 *dst = buf1 + (tid >> 4) * 272 + (tid & 15);  // pad(256 (tid / 16) + tid % 16 + 16 r)
 #pragma unroll
     for (int r = 0; r < 16; ++r) dst[17 * r] = v[r];
