@@ -569,15 +569,16 @@ def run_fdas(args):
     soak = {"steps": soak_steps, "ms_per_step": sa.elapsed_time(sb) / soak_steps, "clocks": soak_sampler.summary()}
 
     # A stream of spectra: the plain convolution and the full harmonic sum of each spectrum, spectra
-    # alternating over two streams and planes, so that one spectrum's harmonic sum (HBM-bound) runs
+    # taking three streams and planes in turn, so that one spectrum's harmonic sum (HBM-bound) runs
     # beside the next one's convolution (ALU-bound). Reported beside the one-stream value.
     pipelined = None
     if "fp32" in searchers:
-        pair = [searchers["fp32"], fdas.Searcher(searchers["fp32"].p, args.n, device=f"cuda:{local}")]
-        streams = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)]
+        pair = [searchers["fp32"]] + [fdas.Searcher(searchers["fp32"].p, args.n, device=f"cuda:{local}")
+                                      for _ in range(2)]
+        streams = [torch.cuda.Stream(dev) for _ in range(3)]
 
         def pstep(k):
-            s2, st = pair[k & 1], streams[k & 1]
+            s2, st = pair[k % 3], streams[k % 3]
             fdas.fdas_convolve(s2.p, d_spec, args.n, s2.tmpl, s2.plane, s2.ld, st)
             fdas.fdas_harmonic_sum(s2.p, s2.plane, args.n, s2.ld, s2.thresh, s2.cands, s2.counts, s2.peaks, s2.ws,
                                    s2.ws_bytes, st)
@@ -600,10 +601,10 @@ def run_fdas(args):
         torch.cuda.synchronize(dev)
         barrier()
         p_ms = max_over_ranks(pa.elapsed_time(pb), world, dev)
-        pipelined = {"spectra_per_s": job_throughput(world, args.steps, p_ms / 1e3), "streams": 2,
+        pipelined = {"spectra_per_s": job_throughput(world, args.steps, p_ms / 1e3), "streams": 3,
                      "ms_per_spectrum": p_ms / args.steps, "precision": "fp32",
-                     "path": "fdas_convolve + fdas_harmonic_sum per spectrum, spectra alternating over two "
-                             "streams and planes (the convolution of one overlaps the harmonic sum of the other)"}
+                     "path": "fdas_convolve + fdas_harmonic_sum per spectrum, spectra taking three streams and "
+                             "planes in turn (a convolution overlaps the harmonic sums of the others)"}
         del pair
 
     # End to end from host memory, every step: the pinned spectrum in, the candidates, counts and
