@@ -14,6 +14,9 @@ constexpr int kF = 2048;
 constexpr int kThreads = 128;
 constexpr int kPadded = kF + kF / 16;  // one pad element after every 16
 
+// Padded position of element e of an exchange buffer (one pad element after every 16), conflict-free
+// for 64-bit accesses. The exchanges below address it as one base pointer per thread plus constant
+// offsets (the comments give the pad() expression each one implements).
 __device__ __forceinline__ int pad(int e) { return e + (e >> 4); }
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
@@ -182,8 +185,9 @@ __device__ __forceinline__ constexpr float tan16() {
 }
 
 // 16-point DFT in registers, natural order in and out: the first radix-4 layer and the untwiddled
-// row of the second with packed sums, the three rows with constant twiddles W16^m in FMA form. Same
-// issue slots as dft16 with packed sums, 6 fewer FP32 pipe operations per twiddled row.
+// row of the second with packed sums, the three rows with constant twiddles W16^m in FMA form (about
+// the same issue slots as complex products followed by packed sums, 6 fewer FP32 pipe operations
+// per twiddled row).
 template <bool INV>
 __device__ __forceinline__ void dft16_hyb(float2 (&v)[16]) {
 #pragma unroll
