@@ -25,8 +25,11 @@
 namespace fdas {
 namespace {
 
-// Two exchange buffers, two template buffers, and two mbarriers for the template copies.
-constexpr size_t kSmemBytes = (2 * kPadded + 2 * kF) * sizeof(float2) + 2 * sizeof(unsigned long long);
+// Two exchange buffers, two template buffers, the HP_1 thresholds of the first kTaShared rows, and two
+// mbarriers for the template copies.
+constexpr int kTaShared = 256;
+constexpr size_t kSmemBytes =
+    (2 * kPadded + 2 * kF) * sizeof(float2) + kTaShared * sizeof(float) + 2 * sizeof(unsigned long long);
 
 // HP_1 detection fused into the convolution (fdas_search): HP_1(i, j) is the plane value itself
 // (Algorithm 1 with k = 1), so for the rows that take part in no other plane (|i| > c/2) the
@@ -74,13 +77,17 @@ __global__ void __launch_bounds__(kThreads, 3)
     float2 *buf0 = smem;
     float2 *buf1 = smem + kPadded;
     float2 *tbuf = smem + 2 * kPadded;  // [2][kF], template values of the current and next template
-    unsigned long long *tbar = reinterpret_cast<unsigned long long *>(smem + 2 * kPadded + 2 * kF);
+    float *ta_s = reinterpret_cast<float *>(smem + 2 * kPadded + 2 * kF);  // HP1: TA(1, t) for t < kTaShared
+    unsigned long long *tbar = reinterpret_cast<unsigned long long *>(ta_s + kTaShared);
     const int tid = threadIdx.x;
     if (tid == 0) {
         mbar_init(&tbar[0]);
         mbar_init(&tbar[1]);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
+    if (HP1)
+        for (int t = tid; t < n_temp && t < kTaShared; t += kThreads)
+            ta_s[t] = hp1.ta ? __ldg(&hp1.ta[t]) : __int_as_float(0x7f800000);
     __syncthreads();
     unsigned phase = 0u;  // bit b: parity of the next completion of template buffer b
     const float2 *wtab = tmpl + (size_t)n_temp * kF;  // exp(-2 pi i k / F)
@@ -190,7 +197,7 @@ __global__ void __launch_bounds__(kThreads, 3)
                 }
             }
             if (k1row) {
-                const float ta = hp1.ta ? __ldg(&hp1.ta[t]) : __int_as_float(0x7f800000);
+                const float ta = t < kTaShared ? ta_s[t] : hp1.ta ? __ldg(&hp1.ta[t]) : __int_as_float(0x7f800000);
                 if (__any_sync(0xFFFFFFFFu, mx > ta)) hp1_emit_row(dst, ta, t, col0 + tid, smask, h1);  // rare
                 if (mx > best) {  // strict: the first template wins ties, as in the canonical order
                     best = mx;
