@@ -46,8 +46,8 @@ KERNEL_SOURCES = {
 # "harmonic.cu": the harmonic stage of an FP32 search (no single-plane launch); "harmonic.cu+k1":
 # the full harmonic sum, as the tensor-core forms run it.
 NCU_TRAFFIC = {
-    "convolve.cu": ("0af2d0624c31", 681.9e6),
-    "convolve_tc.cu": ("f72553a64fe0", 670.7e6),
+    "convolve.cu": ("9be72b55dc87", 682.1e6),
+    "convolve_tc.cu": ("f72553a64fe0", 670.0e6),
     "harmonic.cu": ("a419de2895ad", 1262.2e6),
     "harmonic.cu+k1": ("a419de2895ad", 1612.7e6),
 }
