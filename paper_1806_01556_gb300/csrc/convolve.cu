@@ -224,32 +224,6 @@ __global__ void __launch_bounds__(kThreads, 3)
 
 }  // namespace
 
-// The last wave of a grid of whole-segment items covers R = n_seg mod slots segments and leaves the
-// other slots idle. Split those R segments into T items of ceil(n_temp / T) templates when that
-// shortens the wave: it then takes ceil(R T / slots) rounds of ceil(n_temp / T) + 1 template
-// transforms (the +1 is each item's forward FFT), against n_temp + 1.
-static void tail_split(int n_seg, int n_temp, int slots, int *head_seg, int *tail_chunks, int *tail_tc) {
-    *head_seg = n_seg;
-    *tail_chunks = 1;
-    *tail_tc = n_temp;
-    if (slots <= 0) return;
-    const int r = n_seg % slots;
-    if (r == 0) return;
-    long long best = (long long)(n_temp + 1);
-    for (int t = 2; t <= 8 && t <= n_temp; ++t) {
-        const int tc = (n_temp + t - 1) / t;
-        const int chunks = (n_temp + tc - 1) / tc;
-        const long long rounds = ((long long)r * chunks + slots - 1) / slots;
-        const long long cost = rounds * (tc + 1);
-        if (cost < best) {
-            best = cost;
-            *head_seg = n_seg - r;
-            *tail_chunks = chunks;
-            *tail_tc = tc;
-        }
-    }
-}
-
 static void chunking(const Geometry &g, int templates_per_item, int *t_chunk, int *n_tchunk) {
     if (templates_per_item <= 0 && g.precision != FDAS_FP32) templates_per_item = kTcDefaultTemplatesPerItem;
     *t_chunk = (templates_per_item > 0 && templates_per_item < g.n_temp) ? templates_per_item : g.n_temp;
@@ -278,9 +252,6 @@ cudaError_t launch_convolve_fp32(const Geometry &g, const float2 *spec, size_t n
     jobs.n_seg = (int)((n + g.keep - 1) / g.keep);
     jobs.n_temp = g.n_temp;
     chunking(g, templates_per_item, &jobs.t_chunk, &jobs.n_tchunk);
-    jobs.head_seg = jobs.n_seg;
-    jobs.tail_chunks = jobs.n_tchunk;
-    jobs.tail_tc = jobs.t_chunk;
     int grid = 0;
     cudaError_t e = persistent_grid(jobs.n_seg * jobs.n_tchunk, ctas_per_sm, &grid);
     if (e != cudaSuccess) return e;
@@ -333,24 +304,10 @@ cudaError_t launch_convolve_hp1(const Geometry &g, const float2 *spec, size_t n,
     cudaError_t e = cudaFuncSetAttribute(fdas_ols_fp32<true, SingleJobs>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kSmemBytes);
     if (e != cudaSuccess) return e;
-    // One item per CTA; the segments of the last partial wave are split by templates (tail_split).
-    int dev = 0, sms = 0, per_sm = 0;
-    e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fdas_ols_fp32<true, SingleJobs>, kThreads,
-                                                          kSmemBytes);
-    if (e != cudaSuccess) return e;
-    tail_split(jobs.n_seg, g.n_temp, sms * per_sm, &jobs.head_seg, &jobs.tail_chunks, &jobs.tail_tc);
-    if (jobs.n_tchunk != 1) {  // templates already chunked: no tail split
-        jobs.head_seg = jobs.n_seg;
-        jobs.tail_chunks = jobs.n_tchunk;
-        jobs.tail_tc = jobs.t_chunk;
-    }
     // The single-plane rows: |i| > c/2 with two or more planes, every row with one.
     const Hp1 hp1{(harm_mask & 1u) ? thresh : nullptr, ws.raw, ws.counters, ws.peaks, g.c, n_harm >= 2 ? g.c / 2 + 1 : 0};
-    const int items = jobs.head_seg * jobs.n_tchunk + (jobs.n_seg - jobs.head_seg) * jobs.tail_chunks;
-    fdas_ols_fp32<true><<<items, kThreads, kSmemBytes, s>>>(jobs, tmpl, g.n_temp, g.h, g.keep, hp1);
+    fdas_ols_fp32<true><<<jobs.n_seg * jobs.n_tchunk, kThreads, kSmemBytes, s>>>(jobs, tmpl, g.n_temp, g.h, g.keep,
+                                                                                hp1);
     return cudaGetLastError();
 }
 

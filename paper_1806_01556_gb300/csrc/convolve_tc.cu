@@ -421,9 +421,6 @@ cudaError_t launch_convolve_tc(const Geometry &g, const float2 *spec, size_t n, 
     const int tpi = templates_per_item > 0 ? templates_per_item : kTcDefaultTemplatesPerItem;
     jobs.t_chunk = tpi < g.n_temp ? tpi : g.n_temp;
     jobs.n_tchunk = (g.n_temp + jobs.t_chunk - 1) / jobs.t_chunk;
-    jobs.head_seg = jobs.n_seg;
-    jobs.tail_chunks = jobs.n_tchunk;
-    jobs.tail_tc = jobs.t_chunk;
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

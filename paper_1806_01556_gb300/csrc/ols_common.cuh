@@ -274,10 +274,7 @@ struct Item {
     unsigned long long *raw;
 };
 
-// Work items of a single spectrum. Segments s < head_seg: item = s * n_tchunk + chunk, t_chunk
-// templates each. The segments after them (the last, partial wave of the grid) are split finer, into
-// tail_chunks items of tail_tc templates, so that the wave fills the GPU; head_seg = n_seg when no
-// segment is split.
+// Work items of a single spectrum: item = s * n_tchunk + chunk.
 struct SingleJobs {
     const float2 *spec;
     float *plane;
@@ -287,21 +284,11 @@ struct SingleJobs {
     int t_chunk;
     int n_tchunk;
     int n_temp;
-    int head_seg;
-    int tail_chunks;
-    int tail_tc;
-    __device__ int total() const { return head_seg * n_tchunk + (n_seg - head_seg) * tail_chunks; }
+    __device__ int total() const { return n_seg * n_tchunk; }
     __device__ Item get(int item) const {
-        const int head = head_seg * n_tchunk;
-        if (item < head) {
-            const int s = item / n_tchunk;
-            const int t0 = (item - s * n_tchunk) * t_chunk;
-            return Item{spec, plane, ld, n, s, t0, min(t0 + t_chunk, n_temp), nullptr, nullptr, nullptr};
-        }
-        const int k = item - head;
-        const int s = head_seg + k / tail_chunks;
-        const int t0 = (k - (s - head_seg) * tail_chunks) * tail_tc;
-        return Item{spec, plane, ld, n, s, t0, min(t0 + tail_tc, n_temp), nullptr, nullptr, nullptr};
+        const int s = item / n_tchunk;
+        const int t0 = (item - s * n_tchunk) * t_chunk;
+        return Item{spec, plane, ld, n, s, t0, min(t0 + t_chunk, n_temp), nullptr, nullptr, nullptr};
     }
 };
 
