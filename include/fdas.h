@@ -318,8 +318,8 @@ fdas_status fdas_search_host(const fdas_params *p, const void *h_spec, size_t n,
  * not change before then. Everything is ordered on `stream` alone, so the copy in waits for the
  * stream's previous work. With pinned host buffers and three sets of device buffers used on three
  * streams in turn, each copy in waits only for a search two spectra back and overlaps the other
- * streams' searches (at N = 2^21 on a GB300: 1428 spectra/s end to end, the device-resident rate;
- * with two streams about half of each copy stays exposed). Arguments and checks as in
+ * streams' searches (at N = 2^21 on a GB300 the end-to-end rate then matches the device-resident
+ * one; with two streams about half of each copy stays exposed). Arguments and checks as in
  * fdas_search_host.
  */
 fdas_status fdas_search_host_async(const fdas_params *p, const void *h_spec, size_t n, void *d_spec,
