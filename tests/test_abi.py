@@ -297,6 +297,27 @@ def test_bench_path_roofline_is_the_slower_floor():
     assert fast["bound"] == "alu" and fast["ms_at_roofline"] == fast["ms_flop"]
 
 
+def test_bench_algorithmic_work_at_2_21():
+    """bench.py's algorithmic work per 2^21-bin spectrum, against the counts of the method: 1289
+    segments of L = 2048 - 420 = 1628 outputs; one forward and 85 inverse 2048-point FFTs per
+    segment at 5 F log2 F = 112,640 flop each; 85 complex products of 2048 points per segment at 6
+    flop; |y|^2 at 3 flop per plane point; 2048 complex64 read per segment and the 713 MB plane
+    written. The FP32 search's harmonic stage reads the 43 rows with |i| <= 21 again, the split forms
+    all 85."""
+    import bench
+
+    n = 1 << 21
+    alg = bench.algorithmic(n)
+    assert alg["n_seg"] == 1289 and (1289 - 1) * 1628 < n <= 1289 * 1628
+    fft = 112_640
+    want = 1289 * fft + 85 * 1289 * fft + 85 * 1289 * 2048 * 6 + 85 * n * 3
+    assert alg["conv_flop"] == want and abs(want - 1.4368e10) < 1e7
+    assert alg["conv_bytes"] == 1289 * 2048 * 8 + 85 * n * 4
+    assert alg["hs_bytes"] == 85 * n * 4 == 713_031_680
+    assert bench.hs_rows("fp32") == 43 and bench.hs_rows("bf16x3") == 85 and bench.hs_rows("fp16s") == 85
+    assert bench.algorithmic(n, rows_read=43)["hs_bytes"] == 43 * n * 4
+
+
 def test_bench_oracle_pool_equals_the_oracle():
     """The CPU baseline's split of the oracle plane over worker processes (column blocks computed from
     bins widened by the half width) equals the oracle's plane_ols on the whole spectrum, and the
